@@ -1,0 +1,417 @@
+"""Throughput of the Ehrenfest-regularised D2Q9 step on one GB300 (or N
+replicas), printed as one JSON line.
+
+Workload (default): square cylinder of side L = 128 in a 4096 x 2048
+free-slip channel, Re = 20000, inflow u = 0.05 with seeded 1e-4 noise,
+polynomial equilibrium, delta = 1e-3, k = 16, populations stored in plain
+FP32.  One bench step = one lattice time step of the whole hot path:
+pull-stream + collide + dS + block top-k (one kernel) and global select +
+Ehrenfests' step (one single-block kernel).
+
+  python bench.py [--steps K] [--warmup W] [--precision f32|f32dev|f16dev|f64]
+  python bench.py --impl reference     # the FP64 CPU oracle as the reference arm
+  torchrun --nproc-per-node N bench.py --gpus N   # N independent replicas
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_0705_4371_gb300 import inputs  # noqa: E402
+
+METRIC = ("D2Q9 MLUPS incl. Ehrenfest filter, % HBM roofline; chosen vs plain at equal error")
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "source": "fallback"}
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_collide_d2q9_traffic.json")
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_0705_4371_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as fh:
+                h.update(name.encode())
+                h.update(fh.read())
+    return h.hexdigest()
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            p = json.load(fh)
+        return {"hbm_gbs": float(p["hbm_gbs"]), "source": "measured"}
+    return dict(PEAKS_FALLBACK)
+
+
+def traffic_per_launch(precision, n_sites):
+    """DRAM bytes per launch of the stream-collide kernel from the committed
+    ncu summary, scaled to n_sites; None if absent or the kernels changed."""
+    if not os.path.exists(PROFILE_SUMMARY):
+        return None
+    with open(PROFILE_SUMMARY) as fh:
+        s = json.load(fh)
+    if s.get("source_sha256") != kernel_source_hash():
+        return None
+    e = s.get("precisions", {}).get(precision)
+    if not e:
+        return None
+    return e["dram_bytes_per_site"] * n_sites
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.2)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        sm, mx, pw = [], [], []
+        for r in rows:
+            try:
+                sm.append(float(r[1])); mx.append(float(r[2])); pw.append(float(r[3]))
+            except ValueError:
+                pass
+            for i, n in enumerate(names):
+                if r[5 + i].lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload_by_name(name):
+    table = {"c3": inputs.workload_c3, "c3_scaled": inputs.workload_c3_scaled,
+             "c2": inputs.workload_c2}
+    if name in table:
+        return table[name]()
+    raise SystemExit("unknown workload %s" % name)
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+
+def run_gpu(args):
+    import torch
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    from paper_0705_4371_gb300 import lbm
+    lbm.load()
+    w = workload_by_name(args.workload)
+    prec = lbm.PRECISIONS[args.precision]
+    stream = torch.cuda.Stream()
+    g = lbm.Lattice.from_workload(w, precision=prec, stream=stream.cuda_stream)
+    if args.tile_shape >= 0:
+        g.set_tile_shape(args.tile_shape)
+    rho, ux, uy = inputs.cylinder_fields(w)
+    g.init_equilibrium(rho, ux, uy)
+    info = g.info()
+    n_sites = w.n_sites
+
+    # spin-up (untimed): leave the equilibrium start so the regulariser works
+    g.step(args.spinup)
+    g.sync()
+    # warm-up with the timed configuration (direct launches + per-kernel events)
+    g.set_timing(True)
+    g.step(args.warmup)
+    g.sync()
+    g.kernel_times(reset=True)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        torch.cuda.synchronize()
+        barrier()
+        ev0.record(stream)
+        g.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    g.sync()
+    ms = ev0.elapsed_time(ev1)
+    kt = g.kernel_times(reset=True)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    counts = g.counts(min(args.steps, 65536))
+    value = world * n_sites * args.steps / (ms * 1e-3) / 1e6
+    coll_ms = kt["collide_ms"] / max(kt["collide_launches"], 1)
+    alg_bytes = info["bytes_per_site"] * n_sites
+    peaks = load_peaks()
+    achieved = alg_bytes / (coll_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
+                "traffic": traffic_per_launch(args.precision, n_sites),
+                "kernel": "k_collide_d2q9", "algorithmic_bytes_per_site": info["bytes_per_site"],
+                "avg_launch_ms": round(coll_ms, 5), "peak_source": peaks["source"] + " hbm_gbs",
+                "step_frac_of_peak": round(alg_bytes * args.steps / (ms * 1e-3) / 1e9 /
+                                           peaks["hbm_gbs"], 4)}
+
+    # e2e through the public C ABI with host buffers: each step uploads the
+    # populations from pinned host memory (lb_set_state), advances one step,
+    # and reads the moments back to pinned host memory (lb_moments).
+    f_host = torch.from_numpy(g.get_state()).pin_memory().numpy()
+    outs = [torch.empty((w.ny, w.nx), dtype=torch.float64).pin_memory().numpy() for _ in range(4)]
+    import ctypes as C
+    lib = lbm.load()
+
+    def e2e_step():
+        lbm._check(lib.lb_set_state(g.h, lbm._ptr(f_host)))
+        lbm._check(lib.lb_step(g.h, 1))
+        lbm._check(lib.lb_moments(g.h, *(lbm._ptr(o) for o in outs), 0))
+
+    g.set_timing(False)
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": round(world * n_sites * args.e2e_steps / e2e_s / 1e6, 2), "unit": "MLUPS",
+           "h2d_bytes_per_step": int(f_host.nbytes),
+           "d2h_bytes_per_step": int(sum(o.nbytes for o in outs)),
+           "steps": args.e2e_steps,
+           "api": "lb_set_state(host f64) + lb_step(1) + lb_moments(host)"}
+
+    # forms beside the headline (same workload, same timing method)
+    forms = {}
+    if args.forms and rank == 0:
+        for fname in ("f32dev", "f16dev"):
+            if fname == args.precision:
+                continue
+            with lbm.Lattice.from_workload(w, precision=lbm.PRECISIONS[fname],
+                                           stream=stream.cuda_stream) as h2:
+                h2.init_equilibrium(rho, ux, uy)
+                h2.step(args.spinup)
+                h2.set_timing(True)
+                h2.step(args.warmup)
+                h2.sync()
+                h2.kernel_times(reset=True)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                h2.step(args.form_steps)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                fms = e0.elapsed_time(e1)
+                k2 = h2.kernel_times(reset=True)
+                inf2 = h2.info()
+                cms = k2["collide_ms"] / max(k2["collide_launches"], 1)
+                ach = inf2["bytes_per_site"] * n_sites / (cms * 1e-3) / 1e9
+                forms[fname] = {"MLUPS": round(n_sites * args.form_steps / (fms * 1e-3) / 1e6, 1),
+                                "ms_per_step": round(fms / args.form_steps, 5),
+                                "collide_GBps": round(ach, 1),
+                                "collide_frac": round(ach / peaks["hbm_gbs"], 4),
+                                "bytes_per_site": inf2["bytes_per_site"]}
+
+    cpu = cpu_baseline(w, args) if (rank == 0 and world == 1 and not args.no_cpu) else None
+    clk = clocks.summary()
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"f32": "f32", "f32dev": "f32", "f16dev": "f32", "f64": "f64"}[args.precision],
+        "data": "synthetic (seeded splitmix64 inflow noise; no dataset)",
+        "config": {"workload": w.name, "lattice": "D2Q9", "nx": w.nx, "ny": w.ny, "L": w.L,
+                   "Re": round(w.L * w.u_in[0] / w.nu, 3), "nu": w.nu,
+                   "equilibrium": "polynomial", "storage": args.precision,
+                   "delta": w.delta, "k": w.k, "spinup_steps": args.spinup,
+                   "l2": "inputs larger than L2 (two population buffers of %d MB each)"
+                         % (info["bytes_per_pop"] * 9 * info["nxp"] * w.ny // 2 ** 20),
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "timing": "CUDA events on the library stream; direct launches with "
+                             "per-kernel events"},
+        "roofline": roofline,
+        "ehrenfest_sites_per_step_mean": round(float(np.mean(counts)), 3),
+        "e2e": e2e,
+        "gpu_launches": int(kt["collide_launches"] + kt["select_launches"]),
+        "launch_structure": "one launch per step; global select + Ehrenfests' step in its last block",
+        "clocks": clk,
+        "cpu_baseline": cpu,
+        "forms": forms or None,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    g.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------------------------
+# CPU oracle: the reported baseline and the reference arm
+# --------------------------------------------------------------------------
+
+def _oracle_setup(w):
+    from oracle import core as ora
+    cfg = ora.Config(w.lattice, w.nx, w.ny, w.eq, ora.beta_of_nu(w.nu), w.delta, w.k, w.bc,
+                     w.rho_in, w.u_in, w.obstacle)
+    rho, ux, uy = inputs.cylinder_fields(w)
+    f = ora.init_field(cfg, rho, ux, uy)
+    return ora, cfg, f
+
+
+def cpu_baseline(w, args):
+    """The oracle as it stands on the host cores, on a bounded sample of the
+    same workload: whole steps of the full grid for ~args.cpu_seconds."""
+    ora, cfg, f = _oracle_setup(w)
+    ora.run(cfg, f, 1, log_selection=False)          # first touch
+    n, t = 0, 0.0
+    while t < args.cpu_seconds and n < 1000:
+        t0 = time.perf_counter()
+        f, _ = ora.run(cfg, f, 1, log_selection=False)
+        t += time.perf_counter() - t0
+        n += 1
+    return {"value": round(w.n_sites * n / t / 1e6, 3), "unit": "MLUPS",
+            "cores": ora.num_threads(), "kind": "oracle",
+            "sample": "%d whole time steps of the %dx%d grid (%.1f s)" % (n, w.nx, w.ny, t)}
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    from oracle import core as ora
+    w_full = workload_by_name(args.workload)
+    # calibrate the oracle's rate on the 1/8-scaled layout, then take the
+    # largest layout of the same workload family whose K + W steps fit the
+    # time budget
+    cal = inputs.workload_c3_scaled()
+    o, cfg, f = _oracle_setup(cal)
+    t0 = time.perf_counter()
+    o.run(cfg, f, 3, log_selection=False)
+    rate = cal.n_sites * 3 / (time.perf_counter() - t0)
+    budget = args.ref_seconds / max(1, args.steps + args.warmup)
+    cands = [w_full] + [inputs.cylinder(w_full.nx // s, w_full.ny // s, max(4, w_full.L // s),
+                                        20000.0, name="%s_scaled_1_%d" % (w_full.name, s))
+                        for s in (2, 4, 8, 16, 32)]
+    w = next((c for c in cands if c.n_sites / rate <= budget), cands[-1])
+    o, cfg, f = _oracle_setup(w)
+    for _ in range(args.warmup):
+        f, _ = o.run(cfg, f, 1, log_selection=False)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f, _ = o.run(cfg, f, 1, log_selection=False)
+    el = time.perf_counter() - t0
+    value = w.n_sites * args.steps / el / 1e6
+    sample = "each step = one whole oracle time step of the %dx%d layout (L=%d)" % (w.nx, w.ny, w.L)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "MLUPS",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(el * 1e3 / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded splitmix64 inflow noise; no dataset)",
+        "config": {"workload": w_full.name, "lattice": "D2Q9", "nx": w_full.nx, "ny": w_full.ny,
+                   "L": w_full.L, "delta": w_full.delta, "k": w_full.k,
+                   "parallelism": "host cores (OpenMP)"},
+        "cpu_baseline": {"value": round(value, 3), "unit": "MLUPS", "cores": ora.num_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--spinup", type=int, default=200)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c3")
+    ap.add_argument("--precision", default="f32", choices=["f64", "f32", "f32dev", "f16dev"])
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--tile-shape", type=int, default=-1)
+    ap.add_argument("--forms", type=int, default=1)
+    ap.add_argument("--form-steps", type=int, default=2000)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-seconds", type=float, default=150.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,227 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) Ehrenfest-regularised lattice
+ * Boltzmann library (liblbm.so).
+ *
+ * Method: Brownlee, Gorban, Levesley, "Stable simulation of fluid flow with
+ * high-Reynolds number using Ehrenfests' steps" (2007).  One time step is
+ *   free flight (Sec. 3, exact shift on the lattice, Sec. 3.2) with the
+ *   boundary rules of Sec. 4.2, moments M = m(f) (Sec. 2), quasiequilibrium
+ *   f*_M (Sec. 4.1 / Sec. 4.2 / (argmax)), nonequilibrium entropy
+ *   dS = sum_i f_i ln(f_i / f*_i) ((DelS), Sec. 3.3), the LBGK step
+ *   f + 2 beta (f* - f) ((lbgkLB)), and the Ehrenfests' step f <- f* at the
+ *   k sites with the largest dS > delta (all of them if fewer qualify)
+ *   (Sec. 3.2 last paragraph; (ESLB)).
+ *
+ * Conventions for every entry point:
+ *   - All functions are extern "C", never throw, and return an int status:
+ *     LB_OK (0) or a negative LB_ERR_* code; lb_last_error() then gives a
+ *     thread-local message.  Invalid arguments are rejected before any work
+ *     is queued (LB_ERR_ARG).
+ *   - Population arrays exchanged with the caller are FP64, laid out
+ *     [Q][ny][nx] (population plane, row, x fastest), populations in the
+ *     paper's numbering: D1Q3 {rest, left, right} = {0, -1, +1} (Sec. 4.1);
+ *     D2Q9 0 rest, 1..4 E N W S, 5..8 NE NW SW SE (Sec. 4.2).
+ *   - Field arrays (rho, u_x, u_y, 2E, dS) are FP64 [ny][nx]; site index
+ *     = y * nx + x.  Solid (obstacle) sites hold no populations: they read
+ *     back as 0 (dS: NaN) and are never selected.
+ *   - Unless a function says otherwise, pointers are HOST pointers owned by
+ *     the caller and only read / written during the call.  The library owns
+ *     all device memory it allocates (cudaMalloc in lb_create) and frees it
+ *     in lb_destroy.
+ *   - Work is queued on the stream given to lb_create (NULL: the library
+ *     creates its own non-blocking stream).  Calls that return data to host
+ *     memory synchronise that stream.  One handle must not be used from two
+ *     threads at once.
+ *   - Exactly one GPU: the device current at lb_create.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lb_handle lb_handle;
+
+/* Lattices: Sec. 4.1 (D1Q3, velocities {0, -1, +1}) and Sec. 4.2 (D2Q9). */
+enum lb_lattice { LB_D1Q3 = 0, LB_D2Q9 = 1 };
+
+/* Quasiequilibria:
+ *   LB_EQ_POLY      polynomial (Sec. 4.1 formulas; D2Q9 the standard
+ *                   second-order form W_i rho (1 + 3 v.u + 9/2 (v.u)^2 - 3/2 u^2));
+ *   LB_EQ_ENTROPIC  entropic for mass and momentum (Sec. 4.1 closed form,
+ *                   Sec. 4.2 product formula);
+ *   LB_EQ_ENTROPIC_ENERGY      entropic with the energy constraint as well,
+ *                   M = (rho, rho u1, rho u2, 2E) ((argmax), Lagrange form of
+ *                   Sec. 3.3), solved per site by Newton from the polynomial
+ *                   start point (FP32 iterations, FP64 final updates);
+ *   LB_EQ_ENTROPIC_ENERGY_MLP  as above, Newton warm-started by the 4-64-64-4
+ *                   network loaded with lb_set_mlp (BF16 tensor cores). */
+enum lb_equilibrium {
+    LB_EQ_POLY = 0,
+    LB_EQ_ENTROPIC = 1,
+    LB_EQ_ENTROPIC_ENERGY = 2,
+    LB_EQ_ENTROPIC_ENERGY_MLP = 3
+};
+
+/* Storage of the populations in device memory (the arithmetic type is FP64
+ * for LB_F64 and FP32 otherwise):
+ *   LB_F64      f in FP64;  LB_F32  f in FP32;
+ *   LB_F32_DEV  g = f - W_i rho0 (rho0 = 1) in FP32;
+ *   LB_F16_DEV  g = f - W_i rho0 in FP16.
+ * The deviation forms collide in deviation variables and recompute dS in
+ * FP64 for sites whose FP32 dS lies within a relative 1e-3 of delta. */
+enum lb_precision { LB_F64 = 0, LB_F32 = 1, LB_F32_DEV = 2, LB_F16_DEV = 3 };
+
+/* Boundary kinds of the four sides (Sec. 4.2 boundary paragraph):
+ *   LB_BB         half-way bounce-back (no-slip);
+ *   LB_FREESLIP   specular reflection (y sides only);
+ *   LB_INLET_EQ   incoming populations = quasiequilibrium of (rho_in, u_in)
+ *                 (x sides only);
+ *   LB_OUTLET_EQ  incoming populations = quasiequilibrium of the density and
+ *                 velocity of the penultimate column (x sides only);
+ *   LB_PERIODIC   wrap-around (both sides of an axis).
+ * The obstacle is a solid rectangle [x0, x0+w) x [y0, y0+h) (w = 0: none)
+ * with half-way bounce-back on its faces; it must keep at least one fluid
+ * site to the y walls and two columns to an outlet. */
+enum lb_bc { LB_BB = 0, LB_FREESLIP = 1, LB_INLET_EQ = 2, LB_OUTLET_EQ = 3, LB_PERIODIC = 4 };
+
+typedef struct lb_boundaries {
+    int kind_x0, kind_x1, kind_y0, kind_y1;
+    double rho_in;
+    double u_in[2];
+    int obstacle_x0, obstacle_y0, obstacle_w, obstacle_h;
+} lb_boundaries;
+
+/* Status codes. */
+#define LB_OK 0
+#define LB_ERR_ARG (-1)         /* invalid argument; nothing was queued */
+#define LB_ERR_CUDA (-2)        /* a CUDA runtime call failed */
+#define LB_ERR_NONFINITE (-3)   /* a non-finite moment appeared (sticky) */
+#define LB_ERR_NEWTON (-4)      /* a Newton solve missed 1e-12 (sticky) */
+#define LB_ERR_TIMEOUT (-5)     /* a bounded device wait gave up (sticky) */
+#define LB_ERR_OOM (-6)         /* device allocation failed */
+#define LB_ERR_STATE (-7)       /* call not valid in the handle's state */
+
+/* Create a run.  lattice: lb_lattice; nx, ny: grid (ny = 1 for D1Q3;
+ * nx >= 3, ny >= 3 for D2Q9); equilibrium: lb_equilibrium; nu > 0: kinematic
+ * viscosity, giving the LBGK parameter beta = 1 / (1 + 6 nu) (the paper
+ * writes omega = 2 beta in (lbgkLB) and leaves nu(beta) to the standard
+ * relation nu = (1/omega - 1/2)/3); delta: Ehrenfests' tolerance (any real;
+ * dS > delta is strict); k >= 0: Ehrenfests' sites per step (0 turns the
+ * regulariser off); bc: boundaries (NULL: bounce-back on every side, no
+ * obstacle); precision: lb_precision; cuda_stream: a cudaStream_t or NULL.
+ * The populations start at zero; call lb_init_equilibrium or lb_set_state.
+ * On success *out receives the handle. */
+int lb_create(int lattice, int nx, int ny, int equilibrium, double nu, double delta, int k,
+              const lb_boundaries* bc, int precision, void* cuda_stream, lb_handle** out);
+
+/* Free the handle and all its device memory.  NULL is a no-op. */
+void lb_destroy(lb_handle* h);
+
+/* Set the state to the quasiequilibrium of the given fields (Sec. 4.1 and
+ * Sec. 4.2 both start on the quasiequilibrium manifold).  rho, ux: host
+ * [ny][nx]; uy: host [ny][nx] or NULL (D1Q3 / zero); e2: host [ny][nx] or
+ * NULL, the energy 2E for LB_EQ_ENTROPIC_ENERGY* (NULL: isothermal). */
+int lb_init_equilibrium(lb_handle* h, const double* rho, const double* ux, const double* uy,
+                        const double* e2);
+
+/* Pre-collision populations of the current time step, host [Q][ny][nx]
+ * FP64 (checkpoint).  lb_set_state loads them back (resume); a step after
+ * lb_set_state continues exactly as the run that was saved. */
+int lb_get_state(lb_handle* h, double* f);
+int lb_set_state(lb_handle* h, const double* f);
+
+/* Advance n >= 0 time steps.  Asynchronous: work is queued on the stream
+ * and the call returns the sticky status of work already completed. */
+int lb_step(lb_handle* h, int n);
+
+/* Wait for all queued work; return the sticky status. */
+int lb_sync(lb_handle* h);
+
+/* Moments of the current pre-collision state: rho, u_x, u_y and 2E (each
+ * [ny][nx] FP64; uy and e2 may be NULL).  on_device != 0: the pointers are
+ * device pointers and the call does not synchronise. */
+int lb_moments(lb_handle* h, double* rho, double* ux, double* uy, double* e2, int on_device);
+
+/* Sites that took the Ehrenfests' step in the last completed step (order
+ * unspecified).  idx: host array of cap ints; *count receives the number
+ * (which may exceed cap; only cap are written). */
+int lb_selected(lb_handle* h, int* idx, int cap, int* count);
+
+/* Per-step number of Ehrenfests' sites for the last n steps (oldest
+ * first).  At most the log capacity (lb_set_log_capacity) is kept. */
+int lb_counts(lb_handle* h, int* per_step, int n);
+
+/* Velocity probe (Sec. 4.2.1): log u_x of the pre-collision state at (x, y)
+ * once per step.  lb_probe copies the last n samples (oldest first). */
+int lb_set_probe(lb_handle* h, int x, int y);
+int lb_probe(lb_handle* h, double* ux_series, int n);
+
+/* Capacity (steps) of the count and probe logs; default 65536.  Resets
+ * both logs. */
+int lb_set_log_capacity(lb_handle* h, int steps);
+
+/* Nonequilibrium entropy dS (DelS) of the current pre-collision state at
+ * every site, evaluated exactly (no pre-filter) in the run's arithmetic
+ * type.  ds: [ny][nx] FP64, host or (on_device != 0) device. */
+int lb_delta_s(lb_handle* h, double* ds, int on_device);
+
+/* Test hook: the selection rule alone.  Among the n values ds[0..n)
+ * (host FP64), select the k largest with ds > delta (all of them if fewer
+ * qualify), ties to the lower index, through the same block top-k and
+ * global radix-select kernels as lb_step.  idx_out: host array of at least
+ * min(n, k) ints (order unspecified); *count receives the number selected.
+ * Runs on an internal stream and synchronises. */
+int lb_select_only(const double* ds, int n, double delta, int k, int* idx_out, int* count);
+
+/* Test hook: for the next nsteps steps, use the given selections instead of
+ * selecting (replay of another implementation's choices).  counts[t] sites
+ * for step t, their indices concatenated in idx.  Host arrays. */
+int lb_replay_selection(lb_handle* h, const int* counts, const int* idx, int nsteps);
+
+/* Network for LB_EQ_ENTROPIC_ENERGY_MLP: n = lb_mlp_param_count() FP32
+ * parameters (W1[64][4], b1[64], W2[64][64], b2[64], W3[4][64], b3[4],
+ * then the 8 input normalisation constants (mean[4], inv_std[4]) and the
+ * 4 output scales), host array; rounded to BF16 for inference. */
+int lb_mlp_param_count(void);
+int lb_set_mlp(lb_handle* h, const float* params, int n);
+
+/* Newton statistics of the energy forms since the last reset: total
+ * FP32 and FP64 iterations, sites solved, and sites that missed 1e-12. */
+int lb_newton_stats(lb_handle* h, long long* it32, long long* it64, long long* sites,
+                    long long* fails, int reset);
+
+/* Kernel timing for measurement: when enabled, every launch of lb_step (one
+ * per time step: stream-collide with the selection and the Ehrenfests' step
+ * fused into its last block) is bracketed by CUDA events on the run's
+ * stream (graphs are not used).  lb_kernel_times returns the summed
+ * milliseconds and launch counts since the last reset (synchronises); the
+ * select figures count stand-alone select launches, which lb_step no
+ * longer makes. */
+int lb_set_timing(lb_handle* h, int enable);
+int lb_kernel_times(lb_handle* h, double* collide_ms, long long* collide_launches,
+                    double* select_ms, long long* select_launches, int reset);
+
+/* Tile shape of the D2Q9 stream-collide kernel (sites per thread in x,
+ * rows per block, minimum resident blocks per SM): 0 = 1 x 8, 3 (default),
+ * 1 = 1 x 8, 4;  2 = 2 x 8, 2;  3 = 4 x 8, 1.
+ * Results do not depend on the shape; only the speed does (the batched
+ * runner's autotuner picks it per grid). */
+int lb_set_tile_shape(lb_handle* h, int shape);
+
+/* Run facts: out[0] = Q, out[1] = padded row length (elements),
+ * out[2] = bytes per stored population, out[3] = algorithmic bytes per
+ * site update (read Q + write Q populations), out[4] = launches per step
+ * (1).
+ * beta_out (nullable) receives beta. */
+int lb_info(lb_handle* h, long long* out, double* beta_out);
+
+/* Thread-local message of the last failed call ("" if none). */
+const char* lb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,709 @@
+// lbm_api.cu -- C ABI (include/lbm.h): handle lifecycle, argument checks,
+// device memory, step scheduling (direct launches or CUDA graphs), logs and
+// the sticky error word.  All compute runs in the kernels of
+// lbm_kernels_*.cu; this file only allocates, validates and launches.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_device.cuh"
+#include "lbm_internal.h"
+
+using namespace lbm;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+#define CK(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(e_ == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA,     \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+constexpr int kStageCap = 8192;      // candidates staged in shared memory by the select kernel
+constexpr int kGraphSteps = 32;      // steps per captured graph (even: buffers return)
+constexpr int kDefaultLog = 65536;
+
+size_t storage_bytes(int prec) { return prec == LB_F64 ? 8 : (prec == LB_F16_DEV ? 2 : 4); }
+
+}  // namespace
+
+struct lb_handle {
+    int lattice, Q, nx, ny, nxp, eq, prec, k;
+    double nu, beta, delta, rho0;
+    lb_boundaries bc;
+    cudaStream_t stream;
+    bool own_stream;
+    Launchers L;
+    void* buf[2];
+    int cur;                  // buffer holding the current state
+    bool prestream;           // current buffer holds pre-collision populations
+    long long plane;
+    // selection
+    unsigned long long* cand_key;
+    unsigned* cand_idx;
+    unsigned* cand_count;
+    long long cand_cap;
+    int cand_per_block;
+    int* sel_idx;
+    int* sel_count;
+    long long sel_cap;
+    // logs
+    int* count_ring;
+    double* probe_ring;
+    int ring_cap;
+    int probe_x, probe_y;
+    long long* d_step;
+    long long h_step;         // steps queued so far
+    unsigned* d_err;
+    unsigned* h_err;          // pinned copy
+    cudaEvent_t err_ev;
+    bool err_ev_pending;
+    // replay
+    int* replay_cnt;
+    long long* replay_off;
+    int* replay_idx;
+    long long replay_t0, replay_n;
+    // graph of kGraphSteps steps starting from buffer 0 (graph_exec[0]) or 1
+    cudaGraphExec_t graph_exec[2];
+    // timing
+    bool timing;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, int>> ev_pairs[2];   // (start, stop) indices per kind
+    size_t ev_next;
+    double acc_ms[2];
+    long long acc_n[2];
+    // energy form
+    float* mlp;
+    unsigned long long* newton_stats;
+    // completion ticket of the stream-collide blocks; tile shape of K1
+    unsigned* ticket;
+    int tile_shape;
+};
+
+namespace {
+
+Params make_params(const lb_handle* h, int src, bool prestream) {
+    Params P;
+    memset(&P, 0, sizeof(P));
+    P.nx = h->nx; P.ny = h->ny; P.nxp = h->nxp; P.plane = h->plane;
+    P.eq = h->eq; P.beta = h->beta; P.delta = h->delta; P.rho0 = h->rho0; P.k = h->k;
+    P.bc[0] = h->bc.kind_x0; P.bc[1] = h->bc.kind_x1; P.bc[2] = h->bc.kind_y0; P.bc[3] = h->bc.kind_y1;
+    P.rho_in = h->bc.rho_in; P.ux_in = h->bc.u_in[0]; P.uy_in = h->bc.u_in[1];
+    P.ox0 = h->bc.obstacle_x0; P.oy0 = h->bc.obstacle_y0; P.ow = h->bc.obstacle_w; P.oh = h->bc.obstacle_h;
+    P.src = h->buf[src];
+    P.dst = h->buf[1 - src];
+    P.prestream = prestream ? 1 : 0;
+    P.cand_key = h->cand_key; P.cand_idx = h->cand_idx; P.cand_count = h->cand_count;
+    P.cand_per_block = h->cand_per_block;
+    P.sel_idx = h->sel_idx; P.sel_count = h->sel_count;
+    P.count_ring = h->count_ring; P.probe_ring = h->probe_x >= 0 ? h->probe_ring : nullptr;
+    P.ring_cap = h->ring_cap; P.probe_x = h->probe_x; P.probe_y = h->probe_y;
+    P.step = h->d_step; P.err = h->d_err;
+    P.replay_cnt = h->replay_cnt; P.replay_off = h->replay_off; P.replay_idx = h->replay_idx;
+    P.replay_t0 = h->replay_t0; P.replay_n = h->replay_n;
+    P.recheck = (h->prec == LB_F32_DEV || h->prec == LB_F16_DEV) ? 1 : 0;
+    P.mlp = h->mlp; P.newton_stats = h->newton_stats;
+    P.ticket = h->ticket;
+    return P;
+}
+
+void drop_graphs(lb_handle* h) {
+    for (int i = 0; i < 2; i++) {
+        if (h->graph_exec[i]) cudaGraphExecDestroy(h->graph_exec[i]);
+        h->graph_exec[i] = nullptr;
+    }
+}
+
+int check_sticky(lb_handle* h, bool wait) {
+    if (h->err_ev_pending) {
+        cudaError_t q = wait ? cudaEventSynchronize(h->err_ev) : cudaEventQuery(h->err_ev);
+        if (q == cudaErrorNotReady) return LB_OK;
+        CK(q);
+    }
+    const unsigned e = *h->h_err;
+    if (e & ERR_NONFINITE) return fail(LB_ERR_NONFINITE, "non-finite moments appeared");
+    if (e & ERR_NEWTON) return fail(LB_ERR_NEWTON, "a Newton solve did not reach 1e-12");
+    if (e & ERR_TIMEOUT) return fail(LB_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (e & ERR_REPLAY) return fail(LB_ERR_ARG, "a replayed site index was out of range or solid");
+    return LB_OK;
+}
+
+int queue_err_readback(lb_handle* h) {
+    CK(cudaMemcpyAsync(h->h_err, h->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaEventRecord(h->err_ev, h->stream));
+    h->err_ev_pending = true;
+    return LB_OK;
+}
+
+cudaEvent_t next_event(lb_handle* h) {
+    if (h->ev_next >= h->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        h->ev_pool.push_back(e);
+    }
+    return h->ev_pool[h->ev_next++];
+}
+
+// Queue one time step reading buffer src: a single launch (the last block
+// of the stream-collide kernel performs the selection and the Ehrenfests'
+// step).
+int queue_step(lb_handle* h, int src, bool prestream, bool timed) {
+    const Params P = make_params(h, src, prestream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (timed) {
+        e0 = next_event(h);
+        e1 = next_event(h);
+        if (!e0 || !e1) return fail(LB_ERR_CUDA, "cudaEventCreate failed");
+        CK(cudaEventRecord(e0, h->stream));
+    }
+    CK(h->L.collide(P, h->tile_shape, h->stream));
+    if (timed) {
+        CK(cudaEventRecord(e1, h->stream));
+        h->ev_pairs[0].push_back({(int)h->ev_next - 2, (int)h->ev_next - 1});
+    }
+    return LB_OK;
+}
+
+int build_graph(lb_handle* h, int start) {
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = LB_OK;
+    int src = start;
+    for (int s = 0; s < kGraphSteps && rc == LB_OK; s++) {
+        rc = queue_step(h, src, false, false);
+        src = 1 - src;
+    }
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    if (rc != LB_OK) { if (g) cudaGraphDestroy(g); return rc; }
+    CK(e);
+    e = cudaGraphInstantiate(&h->graph_exec[start], g, 0);
+    cudaGraphDestroy(g);
+    CK(e);
+    return LB_OK;
+}
+
+bool valid_kind(int k) { return k >= LB_BB && k <= LB_PERIODIC; }
+
+}  // namespace
+
+extern "C" {
+
+const char* lb_last_error(void) { return g_last_error.c_str(); }
+
+void lb_destroy(lb_handle* h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    drop_graphs(h);
+    void* ptrs[] = {h->buf[0], h->buf[1], h->cand_key, h->cand_idx, h->cand_count, h->sel_idx,
+                    h->sel_count, h->count_ring, h->probe_ring, h->d_step, h->d_err, h->replay_cnt,
+                    h->replay_off, h->replay_idx, h->mlp, h->newton_stats, h->ticket};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (h->h_err) cudaFreeHost(h->h_err);
+    if (h->err_ev) cudaEventDestroy(h->err_ev);
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+int lb_create(int lattice, int nx, int ny, int equilibrium, double nu, double delta, int k,
+              const lb_boundaries* bc, int precision, void* cuda_stream, lb_handle** out) {
+    if (!out) return fail(LB_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (lattice != LB_D1Q3 && lattice != LB_D2Q9) return fail(LB_ERR_ARG, "unknown lattice %d", lattice);
+    if (equilibrium < LB_EQ_POLY || equilibrium > LB_EQ_ENTROPIC_ENERGY_MLP)
+        return fail(LB_ERR_ARG, "unknown equilibrium %d", equilibrium);
+    if (equilibrium >= LB_EQ_ENTROPIC_ENERGY)
+        return fail(LB_ERR_ARG, "energy-constrained equilibria are not available in this build");
+    if (precision < LB_F64 || precision > LB_F16_DEV) return fail(LB_ERR_ARG, "unknown precision %d", precision);
+    if (!(nu > 0.0) || !(nu < 1e30)) return fail(LB_ERR_ARG, "nu must be positive and finite");
+    if (delta != delta) return fail(LB_ERR_ARG, "delta is NaN");
+    if (k < 0) return fail(LB_ERR_ARG, "k must be >= 0");
+    if (lattice == LB_D1Q3 && ny != 1) return fail(LB_ERR_ARG, "D1Q3 needs ny = 1");
+    if (nx < 3 || (lattice == LB_D2Q9 && ny < 3)) return fail(LB_ERR_ARG, "grid too small");
+    if ((long long)nx * ny >= (1ll << 31)) return fail(LB_ERR_ARG, "grid too large (>= 2^31 sites)");
+    lb_boundaries b;
+    if (bc) b = *bc;
+    else {
+        memset(&b, 0, sizeof(b));
+        b.kind_x0 = b.kind_x1 = b.kind_y0 = b.kind_y1 = LB_BB;
+        b.rho_in = 1.0;
+    }
+    int kinds[4] = {b.kind_x0, b.kind_x1, b.kind_y0, b.kind_y1};
+    for (int i = 0; i < 4; i++)
+        if (!valid_kind(kinds[i])) return fail(LB_ERR_ARG, "unknown boundary kind %d", kinds[i]);
+    if (b.kind_x0 == LB_FREESLIP || b.kind_x1 == LB_FREESLIP)
+        return fail(LB_ERR_ARG, "free-slip is supported on the y sides only");
+    if (b.kind_y0 == LB_INLET_EQ || b.kind_y0 == LB_OUTLET_EQ || b.kind_y1 == LB_INLET_EQ ||
+        b.kind_y1 == LB_OUTLET_EQ)
+        return fail(LB_ERR_ARG, "inlet/outlet are supported on the x sides only");
+    if ((b.kind_x0 == LB_PERIODIC) != (b.kind_x1 == LB_PERIODIC) ||
+        (b.kind_y0 == LB_PERIODIC) != (b.kind_y1 == LB_PERIODIC))
+        return fail(LB_ERR_ARG, "periodic sides come in pairs");
+    if (b.kind_x0 == LB_INLET_EQ || b.kind_x1 == LB_INLET_EQ) {
+        if (!(b.rho_in > 0.0)) return fail(LB_ERR_ARG, "inlet density must be positive");
+        if (!(fabs(b.u_in[0]) < 0.5 && fabs(b.u_in[1]) < 0.5)) return fail(LB_ERR_ARG, "inlet speed too large");
+    }
+    if (b.obstacle_w < 0 || b.obstacle_h < 0) return fail(LB_ERR_ARG, "negative obstacle size");
+    if (b.obstacle_w > 0) {
+        if (lattice == LB_D1Q3) return fail(LB_ERR_ARG, "no obstacle on D1Q3");
+        if (b.obstacle_h <= 0) return fail(LB_ERR_ARG, "obstacle height must be positive");
+        if (b.obstacle_x0 < 1 || b.obstacle_x0 + b.obstacle_w > nx - 3 || b.obstacle_y0 < 1 ||
+            b.obstacle_y0 + b.obstacle_h > ny - 1)
+            return fail(LB_ERR_ARG, "obstacle must keep one fluid site to the walls and two columns to x = nx-1");
+    }
+
+    lb_handle* h = new lb_handle();   // value-initialised: every scalar and pointer is zero
+    h->lattice = lattice; h->Q = lattice == LB_D1Q3 ? 3 : 9; h->nx = nx; h->ny = ny;
+    h->nxp = (nx + 31) / 32 * 32;
+    h->eq = equilibrium; h->prec = precision; h->k = k; h->nu = nu; h->delta = delta;
+    h->beta = 1.0 / (1.0 + 6.0 * nu);
+    h->rho0 = (precision == LB_F32_DEV || precision == LB_F16_DEV) ? 1.0 : 0.0;
+    h->bc = b;
+    h->plane = (long long)ny * h->nxp;
+    h->probe_x = h->probe_y = -1;
+    h->ring_cap = kDefaultLog;
+    h->replay_t0 = -1;
+    if (precision == LB_F64) h->L = launchers_f64(lattice, equilibrium);
+    else if (precision == LB_F16_DEV) h->L = launchers_f16(lattice, equilibrium);
+    else h->L = launchers_f32(lattice, equilibrium);
+
+#define CKH(call)                                                                   \
+    do {                                                                            \
+        cudaError_t e_ = (call);                                                    \
+        if (e_ != cudaSuccess) {                                                    \
+            int rc_ = fail(e_ == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA, \
+                           "%s: %s", #call, cudaGetErrorString(e_));                \
+            lb_destroy(h);                                                          \
+            return rc_;                                                             \
+        }                                                                           \
+    } while (0)
+
+    if (cuda_stream) {
+        h->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        CKH(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+        h->own_stream = true;
+    }
+    const size_t pop_bytes = (size_t)h->Q * h->plane * storage_bytes(precision);
+    for (int i = 0; i < 2; i++) {
+        CKH(cudaMalloc(&h->buf[i], pop_bytes));
+        CKH(cudaMemsetAsync(h->buf[i], 0, pop_bytes, h->stream));
+    }
+    const long long nsites = (long long)nx * ny;
+    // candidate capacity: blocks x min(k, sites per block), largest over the
+    // tile shapes (D2Q9) or the one-site-per-thread kernel (D1Q3)
+    long long cap = 0;
+    if (lattice == LB_D2Q9) {
+        const int vecs[] = {1, 1, 2, 4}, rows[] = {8, 8, 8, 8};
+        for (int s = 0; s < kTileShapes; s++) {
+            const long long tx = 32ll * vecs[s], per = tx * rows[s];
+            const long long nb = ((nx + tx - 1) / tx) * ((ny + rows[s] - 1) / rows[s]);
+            cap = std::max(cap, nb * std::min((long long)k, per));
+        }
+    } else {
+        cap = ((nsites + 255) / 256) * std::min((long long)k, 256ll);
+    }
+    h->cand_per_block = std::min(k, 1024);
+    h->cand_cap = std::max(1ll, cap);
+    h->sel_cap = std::max(1ll, std::min((long long)k, nsites));
+    CKH(cudaMalloc(&h->cand_key, h->cand_cap * sizeof(unsigned long long)));
+    CKH(cudaMalloc(&h->cand_idx, h->cand_cap * sizeof(unsigned)));
+    CKH(cudaMalloc(&h->cand_count, sizeof(unsigned)));
+    CKH(cudaMalloc(&h->sel_idx, std::max(h->sel_cap, (long long)1) * sizeof(int)));
+    CKH(cudaMalloc(&h->sel_count, sizeof(int)));
+    CKH(cudaMalloc(&h->count_ring, h->ring_cap * sizeof(int)));
+    CKH(cudaMalloc(&h->probe_ring, h->ring_cap * sizeof(double)));
+    CKH(cudaMalloc(&h->d_step, sizeof(long long)));
+    CKH(cudaMalloc(&h->d_err, sizeof(unsigned)));
+    CKH(cudaMalloc(&h->newton_stats, 4 * sizeof(unsigned long long)));
+    CKH(cudaMalloc(&h->ticket, sizeof(unsigned)));
+    CKH(cudaMemsetAsync(h->ticket, 0, sizeof(unsigned), h->stream));
+    CKH(cudaMallocHost(&h->h_err, sizeof(unsigned)));
+    *h->h_err = 0;
+    CKH(cudaEventCreateWithFlags(&h->err_ev, cudaEventDisableTiming));
+    CKH(cudaMemsetAsync(h->cand_count, 0, sizeof(unsigned), h->stream));
+    CKH(cudaMemsetAsync(h->sel_count, 0, sizeof(int), h->stream));
+    CKH(cudaMemsetAsync(h->count_ring, 0, h->ring_cap * sizeof(int), h->stream));
+    CKH(cudaMemsetAsync(h->probe_ring, 0, h->ring_cap * sizeof(double), h->stream));
+    CKH(cudaMemsetAsync(h->d_step, 0, sizeof(long long), h->stream));
+    CKH(cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), h->stream));
+    CKH(cudaMemsetAsync(h->newton_stats, 0, 4 * sizeof(unsigned long long), h->stream));
+    CKH(h->L.set_smem(kStageCap));
+    CKH(cudaStreamSynchronize(h->stream));
+    h->cur = 0;
+    h->prestream = true;
+#undef CKH
+    *out = h;
+    return LB_OK;
+}
+
+int lb_init_equilibrium(lb_handle* h, const double* rho, const double* ux, const double* uy,
+                        const double* e2) {
+    if (!h || !rho || !ux) return fail(LB_ERR_ARG, "NULL argument");
+    const long long N = (long long)h->nx * h->ny;
+    for (long long i = 0; i < N; i++)
+        if (!(rho[i] > 0.0) || !(fabs(ux[i]) < 0.5) || (uy && !(fabs(uy[i]) < 0.5)))
+            return fail(LB_ERR_ARG, "init field out of range at site %lld", i);
+    double* d = nullptr;
+    const size_t nb = N * sizeof(double);
+    CK(cudaMallocAsync(&d, 4 * nb, h->stream));
+    CK(cudaMemcpyAsync(d, rho, nb, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(d + N, ux, nb, cudaMemcpyHostToDevice, h->stream));
+    if (uy) CK(cudaMemcpyAsync(d + 2 * N, uy, nb, cudaMemcpyHostToDevice, h->stream));
+    if (e2) CK(cudaMemcpyAsync(d + 3 * N, e2, nb, cudaMemcpyHostToDevice, h->stream));
+    Params P = make_params(h, 1 - h->cur, true);   // dst = buf[cur]
+    CK(h->L.init_eq(P, d, d + N, uy ? d + 2 * N : nullptr, e2 ? d + 3 * N : nullptr, h->stream));
+    CK(cudaFreeAsync(d, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->prestream = true;
+    return LB_OK;
+}
+
+int lb_set_state(lb_handle* h, const double* f) {
+    if (!h || !f) return fail(LB_ERR_ARG, "NULL argument");
+    const long long N = (long long)h->nx * h->ny;
+    const size_t nb = (size_t)h->Q * N * sizeof(double);
+    double* d = nullptr;
+    CK(cudaMallocAsync(&d, nb, h->stream));
+    CK(cudaMemcpyAsync(d, f, nb, cudaMemcpyHostToDevice, h->stream));
+    Params P = make_params(h, 1 - h->cur, true);
+    CK(h->L.import_state(P, d, h->stream));
+    CK(cudaFreeAsync(d, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->prestream = true;
+    return LB_OK;
+}
+
+static int export_fields(lb_handle* h, int mode, double* o0, double* o1, double* o2, double* o3,
+                         int on_device) {
+    const long long N = (long long)h->nx * h->ny;
+    const int nout = mode == 0 ? h->Q : (mode == 1 ? 4 : 1);
+    double* outs[4] = {o0, o1, o2, o3};
+    if (on_device) {
+        Params P = make_params(h, h->cur, h->prestream);
+        CK(h->L.export_state(P, mode, o0, o1, o2, o3, h->stream));
+        return LB_OK;
+    }
+    double* d = nullptr;
+    const size_t per = (size_t)N * sizeof(double) * (mode == 0 ? h->Q : 1);
+    CK(cudaMallocAsync(&d, per * (mode == 1 ? 4 : 1), h->stream));
+    Params P = make_params(h, h->cur, h->prestream);
+    double* d0 = d;
+    double* d1 = (mode == 1 && o1) ? d + N : nullptr;
+    double* d2 = (mode == 1 && o2) ? d + 2 * N : nullptr;
+    double* d3 = (mode == 1 && o3) ? d + 3 * N : nullptr;
+    CK(h->L.export_state(P, mode, d0, d1, d2, d3, h->stream));
+    double* dd[4] = {d0, d1, d2, d3};
+    for (int i = 0; i < (mode == 1 ? 4 : 1); i++)
+        if (outs[i] && dd[i]) CK(cudaMemcpyAsync(outs[i], dd[i], per, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaFreeAsync(d, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    (void)nout;
+    return LB_OK;
+}
+
+int lb_get_state(lb_handle* h, double* f) {
+    if (!h || !f) return fail(LB_ERR_ARG, "NULL argument");
+    return export_fields(h, 0, f, nullptr, nullptr, nullptr, 0);
+}
+
+int lb_moments(lb_handle* h, double* rho, double* ux, double* uy, double* e2, int on_device) {
+    if (!h || !rho || !ux) return fail(LB_ERR_ARG, "NULL argument");
+    return export_fields(h, 1, rho, ux, uy, e2, on_device);
+}
+
+int lb_delta_s(lb_handle* h, double* ds, int on_device) {
+    if (!h || !ds) return fail(LB_ERR_ARG, "NULL argument");
+    return export_fields(h, 2, ds, nullptr, nullptr, nullptr, on_device);
+}
+
+int lb_step(lb_handle* h, int n) {
+    if (!h) return fail(LB_ERR_ARG, "NULL handle");
+    if (n < 0) return fail(LB_ERR_ARG, "n must be >= 0");
+    int rc = check_sticky(h, false);
+    if (rc != LB_OK) return rc;
+    int done = 0;
+    const bool replaying = h->replay_n > 0 && h->h_step < h->replay_t0 + h->replay_n;
+    while (done < n) {
+        const bool direct = h->prestream || h->timing || replaying || (n - done) < kGraphSteps;
+        if (direct) {
+            rc = queue_step(h, h->cur, h->prestream, h->timing);
+            if (rc != LB_OK) return rc;
+            h->prestream = false;
+            h->cur = 1 - h->cur;
+            h->h_step++;
+            done++;
+        } else {
+            if (!h->graph_exec[h->cur]) {
+                rc = build_graph(h, h->cur);
+                if (rc != LB_OK) return rc;
+            }
+            CK(cudaGraphLaunch(h->graph_exec[h->cur], h->stream));
+            h->h_step += kGraphSteps;
+            done += kGraphSteps;   // kGraphSteps is even: cur is unchanged
+        }
+    }
+    return queue_err_readback(h);
+}
+
+int lb_sync(lb_handle* h) {
+    if (!h) return fail(LB_ERR_ARG, "NULL handle");
+    CK(cudaStreamSynchronize(h->stream));
+    return check_sticky(h, true);
+}
+
+int lb_selected(lb_handle* h, int* idx, int cap, int* count) {
+    if (!h || !count || (cap > 0 && !idx)) return fail(LB_ERR_ARG, "NULL argument");
+    int c = 0;
+    CK(cudaMemcpyAsync(&c, h->sel_count, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    *count = c;
+    const int m = std::min(c, cap);
+    if (m > 0) {
+        CK(cudaMemcpyAsync(idx, h->sel_idx, m * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+    }
+    return LB_OK;
+}
+
+static int read_ring(lb_handle* h, void* dring, size_t esz, void* out, int n) {
+    if (n < 0 || n > h->ring_cap) return fail(LB_ERR_ARG, "n must be in [0, log capacity]");
+    if ((long long)n > h->h_step) return fail(LB_ERR_ARG, "only %lld steps were run", h->h_step);
+    if (n == 0) return LB_OK;
+    std::vector<char> all((size_t)h->ring_cap * esz);
+    CK(cudaMemcpyAsync(all.data(), dring, all.size(), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (int j = 0; j < n; j++) {
+        const long long t = h->h_step - n + j;
+        memcpy(static_cast<char*>(out) + j * esz, all.data() + (t % h->ring_cap) * esz, esz);
+    }
+    return LB_OK;
+}
+
+int lb_counts(lb_handle* h, int* per_step, int n) {
+    if (!h || (n > 0 && !per_step)) return fail(LB_ERR_ARG, "NULL argument");
+    return read_ring(h, h->count_ring, sizeof(int), per_step, n);
+}
+
+int lb_set_probe(lb_handle* h, int x, int y) {
+    if (!h) return fail(LB_ERR_ARG, "NULL handle");
+    if (x < 0 || x >= h->nx || y < 0 || y >= h->ny) return fail(LB_ERR_ARG, "probe outside the grid");
+    h->probe_x = x;
+    h->probe_y = y;
+    drop_graphs(h);
+    return LB_OK;
+}
+
+int lb_probe(lb_handle* h, double* ux_series, int n) {
+    if (!h || (n > 0 && !ux_series)) return fail(LB_ERR_ARG, "NULL argument");
+    if (h->probe_x < 0) return fail(LB_ERR_STATE, "no probe set");
+    return read_ring(h, h->probe_ring, sizeof(double), ux_series, n);
+}
+
+int lb_set_log_capacity(lb_handle* h, int steps) {
+    if (!h) return fail(LB_ERR_ARG, "NULL handle");
+    if (steps < 1 || steps > (1 << 26)) return fail(LB_ERR_ARG, "capacity out of range");
+    CK(cudaStreamSynchronize(h->stream));
+    int* cr = nullptr;
+    double* pr = nullptr;
+    CK(cudaMalloc(&cr, steps * sizeof(int)));
+    if (cudaMalloc(&pr, steps * sizeof(double)) != cudaSuccess) {
+        cudaFree(cr);
+        return fail(LB_ERR_OOM, "log allocation failed");
+    }
+    cudaMemset(cr, 0, steps * sizeof(int));
+    cudaMemset(pr, 0, steps * sizeof(double));
+    cudaFree(h->count_ring);
+    cudaFree(h->probe_ring);
+    h->count_ring = cr;
+    h->probe_ring = pr;
+    h->ring_cap = steps;
+    drop_graphs(h);
+    return LB_OK;
+}
+
+int lb_replay_selection(lb_handle* h, const int* counts, const int* idx, int nsteps) {
+    if (!h || nsteps < 0 || (nsteps > 0 && !counts)) return fail(LB_ERR_ARG, "bad argument");
+    std::vector<long long> off(std::max(nsteps, 1));
+    long long tot = 0;
+    for (int t = 0; t < nsteps; t++) {
+        if (counts[t] < 0 || counts[t] > h->sel_cap)
+            return fail(LB_ERR_ARG, "replay count %d at step %d outside [0, %lld]", counts[t], t, h->sel_cap);
+        off[t] = tot;
+        tot += counts[t];
+    }
+    if (tot > 0 && !idx) return fail(LB_ERR_ARG, "idx is NULL");
+    CK(cudaStreamSynchronize(h->stream));
+    cudaFree(h->replay_cnt); cudaFree(h->replay_off); cudaFree(h->replay_idx);
+    h->replay_cnt = nullptr; h->replay_off = nullptr; h->replay_idx = nullptr;
+    CK(cudaMalloc(&h->replay_cnt, std::max(nsteps, 1) * sizeof(int)));
+    CK(cudaMalloc(&h->replay_off, std::max(nsteps, 1) * sizeof(long long)));
+    CK(cudaMalloc(&h->replay_idx, std::max(tot, 1ll) * sizeof(int)));
+    if (nsteps) {
+        CK(cudaMemcpy(h->replay_cnt, counts, nsteps * sizeof(int), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(h->replay_off, off.data(), nsteps * sizeof(long long), cudaMemcpyHostToDevice));
+    }
+    if (tot) CK(cudaMemcpy(h->replay_idx, idx, tot * sizeof(int), cudaMemcpyHostToDevice));
+    h->replay_t0 = h->h_step;
+    h->replay_n = nsteps;
+    drop_graphs(h);
+    return LB_OK;
+}
+
+int lb_select_only(const double* ds, int n, double delta, int k, int* idx_out, int* count) {
+    if (!count || n < 0 || k < 0 || (n > 0 && !ds)) return fail(LB_ERR_ARG, "bad argument");
+    if (delta != delta) return fail(LB_ERR_ARG, "delta is NaN");
+    *count = 0;
+    if (n == 0 || k == 0) return LB_OK;
+    if (!idx_out) return fail(LB_ERR_ARG, "idx_out is NULL");
+    cudaStream_t st;
+    CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    const long long blocks = (n + 1023) / 1024;
+    const int per_block = std::min(k, 1024);
+    const long long cap = blocks * per_block;
+    const long long scap = std::min((long long)k, (long long)n);
+    double* d_ds = nullptr;
+    unsigned long long* key = nullptr;
+    unsigned* cid = nullptr;
+    unsigned* ccount = nullptr;
+    int* sel = nullptr;
+    int* scount = nullptr;
+    long long* step = nullptr;
+    unsigned* err = nullptr;
+    cudaError_t e = cudaSuccess;
+    auto ok = [&](cudaError_t x) { if (e == cudaSuccess) e = x; return e == cudaSuccess; };
+    ok(cudaMalloc(&d_ds, n * sizeof(double)));
+    ok(cudaMalloc(&key, cap * sizeof(unsigned long long)));
+    ok(cudaMalloc(&cid, cap * sizeof(unsigned)));
+    ok(cudaMalloc(&ccount, sizeof(unsigned)));
+    ok(cudaMalloc(&sel, scap * sizeof(int)));
+    ok(cudaMalloc(&scount, sizeof(int)));
+    ok(cudaMalloc(&step, sizeof(long long)));
+    ok(cudaMalloc(&err, sizeof(unsigned)));
+    if (e == cudaSuccess) {
+        ok(cudaMemcpyAsync(d_ds, ds, n * sizeof(double), cudaMemcpyHostToDevice, st));
+        ok(cudaMemsetAsync(ccount, 0, sizeof(unsigned), st));
+        ok(cudaMemsetAsync(step, 0, sizeof(long long), st));
+        ok(cudaMemsetAsync(err, 0, sizeof(unsigned), st));
+        Params P;
+        memset(&P, 0, sizeof(P));
+        P.nx = n; P.ny = 1; P.nxp = n; P.plane = n; P.delta = delta; P.k = k;
+        P.cand_key = key; P.cand_idx = cid; P.cand_count = ccount; P.cand_per_block = per_block;
+        P.sel_idx = sel; P.sel_count = scount; P.step = step; P.err = err; P.ring_cap = 1;
+        Launchers L = launchers_f64(LB_D1Q3, LB_EQ_POLY);
+        ok(L.set_smem(kStageCap));
+        ok(launch_emit_from_ds(P, d_ds, n, st));
+        ok(L.select(P, kStageCap, 1, st));
+        int c = 0;
+        ok(cudaMemcpyAsync(&c, scount, sizeof(int), cudaMemcpyDeviceToHost, st));
+        ok(cudaStreamSynchronize(st));
+        if (e == cudaSuccess) {
+            *count = c;
+            if (c > 0) ok(cudaMemcpy(idx_out, sel, std::min<long long>(c, scap) * sizeof(int),
+                                     cudaMemcpyDeviceToHost));
+        }
+    }
+    void* ptrs[] = {d_ds, key, cid, ccount, sel, scount, step, err};
+    for (void* p : ptrs) if (p) cudaFree(p);
+    cudaStreamDestroy(st);
+    if (e != cudaSuccess)
+        return fail(e == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA, "lb_select_only: %s",
+                    cudaGetErrorString(e));
+    return LB_OK;
+}
+
+int lb_mlp_param_count(void) { return 64 * 4 + 64 + 64 * 64 + 64 + 4 * 64 + 4 + 8 + 4; }
+
+int lb_set_mlp(lb_handle* h, const float* params, int n) {
+    if (!h || !params) return fail(LB_ERR_ARG, "NULL argument");
+    if (n != lb_mlp_param_count()) return fail(LB_ERR_ARG, "expected %d parameters", lb_mlp_param_count());
+    return fail(LB_ERR_STATE, "the learned equilibrium is not available in this build");
+}
+
+int lb_newton_stats(lb_handle* h, long long* it32, long long* it64, long long* sites,
+                    long long* fails, int reset) {
+    if (!h) return fail(LB_ERR_ARG, "NULL handle");
+    unsigned long long s[4] = {0, 0, 0, 0};
+    CK(cudaMemcpyAsync(s, h->newton_stats, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (it32) *it32 = (long long)s[0];
+    if (it64) *it64 = (long long)s[1];
+    if (sites) *sites = (long long)s[2];
+    if (fails) *fails = (long long)s[3];
+    if (reset) CK(cudaMemsetAsync(h->newton_stats, 0, sizeof(s), h->stream));
+    return LB_OK;
+}
+
+int lb_set_timing(lb_handle* h, int enable) {
+    if (!h) return fail(LB_ERR_ARG, "NULL handle");
+    h->timing = enable != 0;
+    return LB_OK;
+}
+
+int lb_kernel_times(lb_handle* h, double* collide_ms, long long* collide_launches, double* select_ms,
+                    long long* select_launches, int reset) {
+    if (!h) return fail(LB_ERR_ARG, "NULL handle");
+    CK(cudaStreamSynchronize(h->stream));
+    for (int kind = 0; kind < 2; kind++) {
+        for (auto& pr : h->ev_pairs[kind]) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, h->ev_pool[pr.first], h->ev_pool[pr.second]));
+            h->acc_ms[kind] += ms;
+            h->acc_n[kind] += 1;
+        }
+        h->ev_pairs[kind].clear();
+    }
+    h->ev_next = 0;
+    if (collide_ms) *collide_ms = h->acc_ms[0];
+    if (collide_launches) *collide_launches = h->acc_n[0];
+    if (select_ms) *select_ms = h->acc_ms[1];
+    if (select_launches) *select_launches = h->acc_n[1];
+    if (reset) {
+        h->acc_ms[0] = h->acc_ms[1] = 0.0;
+        h->acc_n[0] = h->acc_n[1] = 0;
+    }
+    return LB_OK;
+}
+
+int lb_set_tile_shape(lb_handle* h, int shape) {
+    if (!h) return fail(LB_ERR_ARG, "NULL handle");
+    if (shape < 0 || shape >= kTileShapes) return fail(LB_ERR_ARG, "tile shape must be in [0, %d)", kTileShapes);
+    if (h->lattice != LB_D2Q9) return fail(LB_ERR_ARG, "tile shapes apply to D2Q9 runs");
+    CK(cudaStreamSynchronize(h->stream));
+    h->tile_shape = shape;
+    drop_graphs(h);
+    return LB_OK;
+}
+
+int lb_info(lb_handle* h, long long* out, double* beta_out) {
+    if (!h || !out) return fail(LB_ERR_ARG, "NULL argument");
+    out[0] = h->Q;
+    out[1] = h->nxp;
+    out[2] = (long long)storage_bytes(h->prec);
+    out[3] = 2ll * h->Q * (long long)storage_bytes(h->prec);
+    out[4] = 1;
+    if (beta_out) *beta_out = h->beta;
+    return LB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,15 @@
+// Kernel instantiations for storage type double.
+#define LBM_DEFINE_EMIT_FROM_DS
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+Launchers launchers_f64(int lattice, int eq) { return launchers_for<double>(lattice, eq); }
+}  // namespace lbm
+
+namespace lbm {
+cudaError_t launch_emit_from_ds(const Params& P, const double* ds, int n, cudaStream_t st) {
+    const unsigned blocks = (unsigned)((n + 1023) / 1024);
+    k_emit_from_ds<<<blocks > 0 ? blocks : 1, 256, 0, st>>>(P, ds, n);
+    return cudaGetLastError();
+}
+}  // namespace lbm

@@ -1,0 +1,267 @@
+"""Thin ctypes binding of liblbm.so (declared in include/lbm.h).
+
+Argument marshalling only: every step of the lattice Boltzmann path runs in
+the library's CUDA kernels.  ``load()`` raises if the library is missing or
+cannot be loaded; there is no fallback.  Array arguments are numpy FP64
+arrays on the host, or (where the C function takes ``on_device``) CUDA
+device pointers given as integers (e.g. ``torch.Tensor.data_ptr()``).
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblbm.so")
+
+LB_D1Q3, LB_D2Q9 = 0, 1
+LB_EQ_POLY, LB_EQ_ENTROPIC, LB_EQ_ENTROPIC_ENERGY, LB_EQ_ENTROPIC_ENERGY_MLP = 0, 1, 2, 3
+LB_F64, LB_F32, LB_F32_DEV, LB_F16_DEV = 0, 1, 2, 3
+LB_BB, LB_FREESLIP, LB_INLET_EQ, LB_OUTLET_EQ, LB_PERIODIC = 0, 1, 2, 3, 4
+LB_OK, LB_ERR_ARG, LB_ERR_CUDA, LB_ERR_NONFINITE, LB_ERR_NEWTON, LB_ERR_TIMEOUT, LB_ERR_OOM, \
+    LB_ERR_STATE = 0, -1, -2, -3, -4, -5, -6, -7
+
+PRECISIONS = {"f64": LB_F64, "f32": LB_F32, "f32dev": LB_F32_DEV, "f16dev": LB_F16_DEV}
+
+
+class LBError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("liblbm error %d: %s" % (code, msg))
+        self.code = code
+
+
+class lb_boundaries(C.Structure):
+    _fields_ = [("kind_x0", C.c_int), ("kind_x1", C.c_int), ("kind_y0", C.c_int),
+                ("kind_y1", C.c_int), ("rho_in", C.c_double), ("u_in", C.c_double * 2),
+                ("obstacle_x0", C.c_int), ("obstacle_y0", C.c_int), ("obstacle_w", C.c_int),
+                ("obstacle_h", C.c_int)]
+
+
+_lib = None
+
+
+def load(path=None):
+    """Load liblbm.so (raises OSError if it is missing: no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise OSError("liblbm.so not built at %s (run paper_0705_4371_gb300/build.py)" % path)
+    L = C.CDLL(path)
+    vp, ip, dp, fp = C.c_void_p, C.c_int, C.c_double, C.c_float
+    H = C.c_void_p
+    sig = {
+        "lb_create": ([ip, ip, ip, ip, dp, dp, ip, C.POINTER(lb_boundaries), ip, vp, C.POINTER(H)], ip),
+        "lb_destroy": ([H], None),
+        "lb_init_equilibrium": ([H, vp, vp, vp, vp], ip),
+        "lb_get_state": ([H, vp], ip),
+        "lb_set_state": ([H, vp], ip),
+        "lb_step": ([H, ip], ip),
+        "lb_sync": ([H], ip),
+        "lb_moments": ([H, vp, vp, vp, vp, ip], ip),
+        "lb_selected": ([H, vp, ip, C.POINTER(ip)], ip),
+        "lb_counts": ([H, vp, ip], ip),
+        "lb_set_probe": ([H, ip, ip], ip),
+        "lb_probe": ([H, vp, ip], ip),
+        "lb_set_log_capacity": ([H, ip], ip),
+        "lb_delta_s": ([H, vp, ip], ip),
+        "lb_select_only": ([vp, ip, dp, ip, vp, C.POINTER(ip)], ip),
+        "lb_replay_selection": ([H, vp, vp, ip], ip),
+        "lb_mlp_param_count": ([], ip),
+        "lb_set_mlp": ([H, vp, ip], ip),
+        "lb_newton_stats": ([H, vp, vp, vp, vp, ip], ip),
+        "lb_set_timing": ([H, ip], ip),
+        "lb_kernel_times": ([H, vp, vp, vp, vp, ip], ip),
+        "lb_info": ([H, vp, vp], ip),
+        "lb_set_tile_shape": ([H, ip], ip),
+        "lb_last_error": ([], C.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def last_error():
+    return load().lb_last_error().decode()
+
+
+def _check(rc):
+    if rc != LB_OK:
+        raise LBError(rc, last_error())
+    return rc
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return C.c_void_p(a)
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def boundaries(kinds=(LB_BB,) * 4, rho_in=1.0, u_in=(0.0, 0.0), obstacle=(0, 0, 0, 0)):
+    b = lb_boundaries()
+    b.kind_x0, b.kind_x1, b.kind_y0, b.kind_y1 = kinds
+    b.rho_in = rho_in
+    b.u_in[0], b.u_in[1] = u_in
+    b.obstacle_x0, b.obstacle_y0, b.obstacle_w, b.obstacle_h = obstacle
+    return b
+
+
+def select_only(ds, delta, k):
+    """lb_select_only: indices (sorted) of the k largest ds > delta."""
+    L = load()
+    ds = np.ascontiguousarray(ds, np.float64)
+    out = np.zeros(max(1, min(int(k), ds.size)), np.int32)
+    cnt = C.c_int(0)
+    _check(L.lb_select_only(_ptr(ds), ds.size, float(delta), int(k), _ptr(out), C.byref(cnt)))
+    return np.sort(out[:cnt.value].astype(np.int64))
+
+
+def mlp_param_count():
+    return load().lb_mlp_param_count()
+
+
+class Lattice:
+    """One run (a lb_handle).  Mirrors the C calls one to one."""
+
+    def __init__(self, lattice, nx, ny, equilibrium, nu, delta, k, bc=None, precision=LB_F32,
+                 stream=None):
+        self.L = load()
+        self.lattice, self.nx, self.ny = lattice, nx, ny
+        self.q = 3 if lattice == LB_D1Q3 else 9
+        h = C.c_void_p()
+        bptr = C.byref(bc) if bc is not None else None
+        st = C.c_void_p(stream) if stream else None
+        _check(self.L.lb_create(lattice, nx, ny, equilibrium, float(nu), float(delta), int(k),
+                                bptr, precision, st, C.byref(h)))
+        self.h = h
+
+    @classmethod
+    def from_workload(cls, w, precision=LB_F32, stream=None, **over):
+        """Create from a paper_0705_4371_gb300.inputs.Workload."""
+        p = dict(nu=w.nu, delta=w.delta, k=w.k)
+        p.update(over)
+        bc = boundaries(w.bc, w.rho_in, w.u_in, w.obstacle)
+        return cls(w.lattice, w.nx, w.ny, w.eq, p["nu"], p["delta"], p["k"], bc, precision, stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.lb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def shape(self):
+        return (self.ny, self.nx)
+
+    def init_equilibrium(self, rho, ux, uy=None, e2=None):
+        rho, ux, uy, e2 = _f64(rho), _f64(ux), _f64(uy), _f64(e2)
+        _check(self.L.lb_init_equilibrium(self.h, _ptr(rho), _ptr(ux), _ptr(uy), _ptr(e2)))
+
+    def get_state(self):
+        f = np.zeros((self.q, self.ny, self.nx))
+        _check(self.L.lb_get_state(self.h, _ptr(f)))
+        return f
+
+    def set_state(self, f):
+        f = _f64(f)
+        assert f.size == self.q * self.nx * self.ny
+        _check(self.L.lb_set_state(self.h, _ptr(f)))
+
+    def step(self, n=1):
+        return _check(self.L.lb_step(self.h, int(n)))
+
+    def sync(self):
+        return _check(self.L.lb_sync(self.h))
+
+    def moments(self):
+        rho, ux, uy, e2 = (np.zeros(self.shape) for _ in range(4))
+        _check(self.L.lb_moments(self.h, _ptr(rho), _ptr(ux), _ptr(uy), _ptr(e2), 0))
+        return rho, ux, uy, e2
+
+    def moments_device(self, rho_ptr, ux_ptr, uy_ptr=None, e2_ptr=None):
+        _check(self.L.lb_moments(self.h, _ptr(rho_ptr), _ptr(ux_ptr), _ptr(uy_ptr), _ptr(e2_ptr), 1))
+
+    def delta_s(self):
+        ds = np.zeros(self.shape)
+        _check(self.L.lb_delta_s(self.h, _ptr(ds), 0))
+        return ds
+
+    def selected(self, cap=1 << 20):
+        idx = np.zeros(cap, np.int32)
+        cnt = C.c_int(0)
+        _check(self.L.lb_selected(self.h, _ptr(idx), cap, C.byref(cnt)))
+        return np.sort(idx[:min(cnt.value, cap)].astype(np.int64))
+
+    def counts(self, n):
+        out = np.zeros(n, np.int32)
+        _check(self.L.lb_counts(self.h, _ptr(out), int(n)))
+        return out
+
+    def set_probe(self, x, y):
+        _check(self.L.lb_set_probe(self.h, int(x), int(y)))
+
+    def probe(self, n):
+        out = np.zeros(n)
+        _check(self.L.lb_probe(self.h, _ptr(out), int(n)))
+        return out
+
+    def set_log_capacity(self, n):
+        _check(self.L.lb_set_log_capacity(self.h, int(n)))
+
+    def replay_selection(self, selections):
+        counts = np.array([len(s) for s in selections], np.int32)
+        idx = np.concatenate([np.asarray(s, np.int32) for s in selections] + [np.zeros(0, np.int32)])
+        idx = np.ascontiguousarray(idx, np.int32)
+        _check(self.L.lb_replay_selection(self.h, _ptr(counts), _ptr(idx), len(selections)))
+
+    def set_mlp(self, params):
+        p = np.ascontiguousarray(params, np.float32)
+        _check(self.L.lb_set_mlp(self.h, _ptr(p), p.size))
+
+    def newton_stats(self, reset=False):
+        v = [C.c_longlong(0) for _ in range(4)]
+        _check(self.L.lb_newton_stats(self.h, *(C.byref(x) for x in v), int(reset)))
+        return tuple(x.value for x in v)
+
+    def set_timing(self, enable):
+        _check(self.L.lb_set_timing(self.h, int(bool(enable))))
+
+    def kernel_times(self, reset=False):
+        cm, sm = C.c_double(0), C.c_double(0)
+        cn, sn = C.c_longlong(0), C.c_longlong(0)
+        _check(self.L.lb_kernel_times(self.h, C.byref(cm), C.byref(cn), C.byref(sm), C.byref(sn),
+                                      int(reset)))
+        return {"collide_ms": cm.value, "collide_launches": cn.value,
+                "select_ms": sm.value, "select_launches": sn.value}
+
+    def set_tile_shape(self, shape):
+        _check(self.L.lb_set_tile_shape(self.h, int(shape)))
+
+    def info(self):
+        out = np.zeros(5, np.int64)
+        beta = C.c_double(0)
+        _check(self.L.lb_info(self.h, _ptr(out), C.byref(beta)))
+        return {"Q": int(out[0]), "nxp": int(out[1]), "bytes_per_pop": int(out[2]),
+                "bytes_per_site": int(out[3]), "launches_per_step": int(out[4]),
+                "beta": beta.value}
