@@ -31,7 +31,7 @@ from paper_0705_4371_gb300 import inputs  # noqa: E402
 
 METRIC = ("D2Q9 MLUPS incl. Ehrenfest filter, % HBM roofline; chosen vs plain at equal error")
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "source": "fallback"}
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_collide_d2q9_traffic.json")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_collide_d2q9_cylinder4096x2048.md")
 
 
 def kernel_source_hash():
@@ -56,17 +56,21 @@ def load_peaks():
 
 def traffic_per_launch(precision, n_sites):
     """DRAM bytes per launch of the stream-collide kernel from the committed
-    ncu summary, scaled to n_sites; None if absent or the kernels changed."""
+    ncu summary (its traffic_per_site line), scaled to n_sites; None if absent
+    or if the CUDA sources changed since the counters were taken."""
     if not os.path.exists(PROFILE_SUMMARY):
         return None
+    s = None
     with open(PROFILE_SUMMARY) as fh:
-        s = json.load(fh)
-    if s.get("source_sha256") != kernel_source_hash():
+        for line in fh:
+            if line.startswith("traffic_per_site:"):
+                s = json.loads(line.split(":", 1)[1])
+    if not s or s.get("source_sha256") != kernel_source_hash():
         return None
     e = s.get("precisions", {}).get(precision)
     if not e:
         return None
-    return e["dram_bytes_per_site"] * n_sites
+    return int(e["dram_bytes_per_site"] * n_sites)
 
 
 class ClockSampler:

@@ -204,16 +204,17 @@ int lb_kernel_times(lb_handle* h, double* collide_ms, long long* collide_launche
                     double* select_ms, long long* select_launches, int reset);
 
 /* Tile shape of the D2Q9 stream-collide kernel (sites per thread in x,
- * rows per block, minimum resident blocks per SM): 0 = 1 x 8, 3 (default),
- * 1 = 1 x 8, 4;  2 = 2 x 8, 2;  3 = 4 x 8, 1.
+ * warps per block, minimum resident blocks per SM): 0 = 1, 8, 3;
+ * 1 = 1, 8, 4 (default);  2 = 2, 8, 2;  3 = 4, 8, 1.
  * Results do not depend on the shape; only the speed does (the batched
  * runner's autotuner picks it per grid). */
 int lb_set_tile_shape(lb_handle* h, int shape);
 
-/* Run facts: out[0] = Q, out[1] = padded row length (elements),
- * out[2] = bytes per stored population, out[3] = algorithmic bytes per
- * site update (read Q + write Q populations), out[4] = launches per step
- * (1).
+/* Run facts (out: 8 entries): out[0] = Q, out[1] = padded row length
+ * (elements), out[2] = bytes per stored population, out[3] = algorithmic
+ * bytes per site update (read Q + write Q populations), out[4] = launches
+ * per step (1), out[5] = blocks of the persistent stream-collide grid,
+ * out[6] = its resident blocks per SM, out[7] = tile shape.
  * beta_out (nullable) receives beta. */
 int lb_info(lb_handle* h, long long* out, double* beta_out);
 

@@ -41,6 +41,7 @@ int fail(int code, const char* fmt, ...) {
 constexpr int kStageCap = 8192;      // candidates staged in shared memory by the select kernel
 constexpr int kGraphSteps = 32;      // steps per captured graph (even: buffers return)
 constexpr int kDefaultLog = 65536;
+constexpr int kDefaultTileShape = 1;  // fastest measured on GB300 for FP32 / FP16 storage
 
 size_t storage_bytes(int prec) { return prec == LB_F64 ? 8 : (prec == LB_F16_DEV ? 2 : 4); }
 
@@ -97,6 +98,10 @@ struct lb_handle {
     // completion ticket of the stream-collide blocks; tile shape of K1
     unsigned* ticket;
     int tile_shape;
+    // overflow list of sites awaiting an exact dS
+    unsigned* pend_idx;
+    unsigned* pend_count;
+    int grid_blocks, sm_count, blocks_per_sm;
 };
 
 namespace {
@@ -106,6 +111,11 @@ Params make_params(const lb_handle* h, int src, bool prestream) {
     memset(&P, 0, sizeof(P));
     P.nx = h->nx; P.ny = h->ny; P.nxp = h->nxp; P.plane = h->plane;
     P.eq = h->eq; P.beta = h->beta; P.delta = h->delta; P.rho0 = h->rho0; P.k = h->k;
+    P.betaf = (float)h->beta; P.rho0f = (float)h->rho0;
+    // FP32 threshold: the largest float not above delta, so that a site with
+    // FP32 dS > deltaf has dS > delta up to the FP32 rounding of dS itself
+    P.deltaf = (float)h->delta;
+    if ((double)P.deltaf > h->delta) P.deltaf = std::nextafter(P.deltaf, -INFINITY);
     P.bc[0] = h->bc.kind_x0; P.bc[1] = h->bc.kind_x1; P.bc[2] = h->bc.kind_y0; P.bc[3] = h->bc.kind_y1;
     P.rho_in = h->bc.rho_in; P.ux_in = h->bc.u_in[0]; P.uy_in = h->bc.u_in[1];
     P.ox0 = h->bc.obstacle_x0; P.oy0 = h->bc.obstacle_y0; P.ow = h->bc.obstacle_w; P.oh = h->bc.obstacle_h;
@@ -123,6 +133,9 @@ Params make_params(const lb_handle* h, int src, bool prestream) {
     P.recheck = (h->prec == LB_F32_DEV || h->prec == LB_F16_DEV) ? 1 : 0;
     P.mlp = h->mlp; P.newton_stats = h->newton_stats;
     P.ticket = h->ticket;
+    P.pend_idx = h->pend_idx;
+    P.pend_count = h->pend_count;
+    P.grid_blocks = h->grid_blocks;
     return P;
 }
 
@@ -203,6 +216,18 @@ int build_graph(lb_handle* h, int start) {
 
 bool valid_kind(int k) { return k >= LB_BB && k <= LB_PERIODIC; }
 
+// Persistent grid of the stream-collide kernel: resident blocks per SM for
+// the tile shape (occupancy calculator) times the SM count.
+int size_grid(lb_handle* h) {
+    int dev = 0, bps = 1;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev));
+    CK(h->L.occupancy(h->tile_shape, &bps));
+    h->blocks_per_sm = bps < 1 ? 1 : bps;
+    h->grid_blocks = h->blocks_per_sm * h->sm_count;
+    return LB_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -215,7 +240,8 @@ void lb_destroy(lb_handle* h) {
     drop_graphs(h);
     void* ptrs[] = {h->buf[0], h->buf[1], h->cand_key, h->cand_idx, h->cand_count, h->sel_idx,
                     h->sel_count, h->count_ring, h->probe_ring, h->d_step, h->d_err, h->replay_cnt,
-                    h->replay_off, h->replay_idx, h->mlp, h->newton_stats, h->ticket};
+                    h->replay_off, h->replay_idx, h->mlp, h->newton_stats, h->ticket,
+                    h->pend_idx, h->pend_count};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_err) cudaFreeHost(h->h_err);
@@ -240,7 +266,8 @@ int lb_create(int lattice, int nx, int ny, int equilibrium, double nu, double de
     if (k < 0) return fail(LB_ERR_ARG, "k must be >= 0");
     if (lattice == LB_D1Q3 && ny != 1) return fail(LB_ERR_ARG, "D1Q3 needs ny = 1");
     if (nx < 3 || (lattice == LB_D2Q9 && ny < 3)) return fail(LB_ERR_ARG, "grid too small");
-    if ((long long)nx * ny >= (1ll << 31)) return fail(LB_ERR_ARG, "grid too large (>= 2^31 sites)");
+    if ((long long)(lattice == LB_D1Q3 ? 3 : 9) * ny * ((nx + 31) / 32 * 32) >= (1ll << 31))
+        return fail(LB_ERR_ARG, "grid too large (a population array must hold < 2^31 values)");
     lb_boundaries b;
     if (bc) b = *bc;
     else {
@@ -281,6 +308,7 @@ int lb_create(int lattice, int nx, int ny, int equilibrium, double nu, double de
     h->bc = b;
     h->plane = (long long)ny * h->nxp;
     h->probe_x = h->probe_y = -1;
+    h->tile_shape = lattice == LB_D2Q9 ? kDefaultTileShape : 0;
     h->ring_cap = kDefaultLog;
     h->replay_t0 = -1;
     if (precision == LB_F64) h->L = launchers_f64(lattice, equilibrium);
@@ -310,21 +338,10 @@ int lb_create(int lattice, int nx, int ny, int equilibrium, double nu, double de
         CKH(cudaMemsetAsync(h->buf[i], 0, pop_bytes, h->stream));
     }
     const long long nsites = (long long)nx * ny;
-    // candidate capacity: blocks x min(k, sites per block), largest over the
-    // tile shapes (D2Q9) or the one-site-per-thread kernel (D1Q3)
-    long long cap = 0;
-    if (lattice == LB_D2Q9) {
-        const int vecs[] = {1, 1, 2, 4}, rows[] = {8, 8, 8, 8};
-        for (int s = 0; s < kTileShapes; s++) {
-            const long long tx = 32ll * vecs[s], per = tx * rows[s];
-            const long long nb = ((nx + tx - 1) / tx) * ((ny + rows[s] - 1) / rows[s]);
-            cap = std::max(cap, nb * std::min((long long)k, per));
-        }
-    } else {
-        cap = ((nsites + 255) / 256) * std::min((long long)k, 256ll);
-    }
+    // candidate list: one slot per site (warps append every site with
+    // dS > delta; the list can never overflow)
     h->cand_per_block = std::min(k, 1024);
-    h->cand_cap = std::max(1ll, cap);
+    h->cand_cap = std::max(1ll, nsites);
     h->sel_cap = std::max(1ll, std::min((long long)k, nsites));
     CKH(cudaMalloc(&h->cand_key, h->cand_cap * sizeof(unsigned long long)));
     CKH(cudaMalloc(&h->cand_idx, h->cand_cap * sizeof(unsigned)));
@@ -338,6 +355,9 @@ int lb_create(int lattice, int nx, int ny, int equilibrium, double nu, double de
     CKH(cudaMalloc(&h->newton_stats, 4 * sizeof(unsigned long long)));
     CKH(cudaMalloc(&h->ticket, sizeof(unsigned)));
     CKH(cudaMemsetAsync(h->ticket, 0, sizeof(unsigned), h->stream));
+    CKH(cudaMalloc(&h->pend_idx, std::max(1ll, nsites) * sizeof(unsigned)));
+    CKH(cudaMalloc(&h->pend_count, sizeof(unsigned)));
+    CKH(cudaMemsetAsync(h->pend_count, 0, sizeof(unsigned), h->stream));
     CKH(cudaMallocHost(&h->h_err, sizeof(unsigned)));
     *h->h_err = 0;
     CKH(cudaEventCreateWithFlags(&h->err_ev, cudaEventDisableTiming));
@@ -349,6 +369,11 @@ int lb_create(int lattice, int nx, int ny, int equilibrium, double nu, double de
     CKH(cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), h->stream));
     CKH(cudaMemsetAsync(h->newton_stats, 0, 4 * sizeof(unsigned long long), h->stream));
     CKH(h->L.set_smem(kStageCap));
+    if (size_grid(h) != LB_OK) {
+        const std::string msg = g_last_error;
+        lb_destroy(h);
+        return fail(LB_ERR_CUDA, "%s", msg.c_str());
+    }
     CKH(cudaStreamSynchronize(h->stream));
     h->cur = 0;
     h->prestream = true;
@@ -578,9 +603,8 @@ int lb_select_only(const double* ds, int n, double delta, int k, int* idx_out, i
     if (!idx_out) return fail(LB_ERR_ARG, "idx_out is NULL");
     cudaStream_t st;
     CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-    const long long blocks = (n + 1023) / 1024;
     const int per_block = std::min(k, 1024);
-    const long long cap = blocks * per_block;
+    const long long cap = n;
     const long long scap = std::min((long long)k, (long long)n);
     double* d_ds = nullptr;
     unsigned long long* key = nullptr;
@@ -692,7 +716,7 @@ int lb_set_tile_shape(lb_handle* h, int shape) {
     CK(cudaStreamSynchronize(h->stream));
     h->tile_shape = shape;
     drop_graphs(h);
-    return LB_OK;
+    return size_grid(h);
 }
 
 int lb_info(lb_handle* h, long long* out, double* beta_out) {
@@ -702,6 +726,9 @@ int lb_info(lb_handle* h, long long* out, double* beta_out) {
     out[2] = (long long)storage_bytes(h->prec);
     out[3] = 2ll * h->Q * (long long)storage_bytes(h->prec);
     out[4] = 1;
+    out[5] = h->grid_blocks;
+    out[6] = h->blocks_per_sm;
+    out[7] = h->tile_shape;
     if (beta_out) *beta_out = h->beta;
     return LB_OK;
 }

@@ -68,6 +68,7 @@ struct Params {
     long long plane;          // ny * nxp elements
     int eq;
     double beta, delta, rho0;
+    float betaf, deltaf, rho0f;   // the same in FP32 (no FP64 work in FP32 kernels)
     int k;
     int bc[4];
     double rho_in, ux_in, uy_in;
@@ -101,6 +102,11 @@ struct Params {
     unsigned long long* newton_stats;   // it32, it64, sites, fails
     // completion ticket of the stream-collide blocks (the last block selects)
     unsigned* ticket;
+    // sites whose dS the bound could not clear and that did not fit in their
+    // block's shared list (resolved by the last block)
+    unsigned* pend_idx;
+    unsigned* pend_count;
+    int grid_blocks;          // persistent grid size (resident blocks x SMs)
 };
 
 template <int Q, typename T> struct PopArr { T v[Q]; };
@@ -179,6 +185,19 @@ __device__ __forceinline__ void feq_poly(T drho, T rho, T ux, T uy, T* gs) {
         }
     }
 }
+
+// Run parameters in the arithmetic type T.
+template <typename T> struct Par;
+template <> struct Par<float> {
+    __device__ static float beta(const Params& P) { return P.betaf; }
+    __device__ static float delta(const Params& P) { return P.deltaf; }
+    __device__ static float rho0(const Params& P) { return P.rho0f; }
+};
+template <> struct Par<double> {
+    __device__ static double beta(const Params& P) { return P.beta; }
+    __device__ static double delta(const Params& P) { return P.delta; }
+    __device__ static double rho0(const Params& P) { return P.rho0; }
+};
 
 template <typename T> __device__ __forceinline__ T dsqrt(T x);
 template <> __device__ __forceinline__ float dsqrt<float>(float x) { return sqrtf(x); }
@@ -351,7 +370,7 @@ __device__ __forceinline__ unsigned long long ds_key(double d) {
 template <typename L, typename S>
 __device__ void gather_site(const Params& P, int x, int y, typename Store<S>::T* g) {
     using T = typename Store<S>::T;
-    const T rho0 = T(P.rho0);
+    const T rho0 = Par<T>::rho0(P);
     const long long s0 = (long long)y * P.nxp + x;
     if (P.prestream) {
 #pragma unroll
@@ -370,7 +389,7 @@ __device__ void gather_site(const Params& P, int x, int y, typename Store<S>::T*
                 sx = sx < 0 ? sx + P.nx : sx - P.nx;
             } else if (kind == BC_INLET) {
                 if (!have_in) {
-                    feq_rho_u<L, T>(P.eq, T(P.rho_in), T(P.ux_in), T(P.uy_in), rho0, gin);
+                    feq_rho_u<L, T>(P.eq, (T)P.rho_in, (T)P.ux_in, (T)P.uy_in, rho0, gin);
                     have_in = true;
                 }
                 g[i] = gin[i];

@@ -17,6 +17,7 @@ struct Launchers {
     cudaError_t (*export_state)(const Params&, int mode, double*, double*, double*, double*,
                                 cudaStream_t);
     cudaError_t (*set_smem)(int stage_cap);
+    cudaError_t (*occupancy)(int tile_shape, int* blocks_per_sm);
 };
 
 // storage: 0 = FP64, 1 = FP32 (plain and deviation), 2 = FP16 deviation

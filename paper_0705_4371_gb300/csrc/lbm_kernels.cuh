@@ -1,17 +1,19 @@
 // lbm_kernels.cuh -- kernels of one time step (template definitions; each
 // storage type is instantiated in its own translation unit).
 //
-//   k_collide_d2q9   fused pull-stream + moments + f* + dS + LBGK + per-block
-//                    top-k of the Ehrenfests' candidates (the HBM-bound
-//                    kernel; 4 sites per thread, aligned vector loads and
-//                    warp shuffles for the x-shifted planes in the interior)
-//   k_collide_site   the same update, one site per thread (D1Q3 runs)
-//   The last block of each stream-collide launch runs the global radix
-//   select of the k sites with the largest dS > delta over the block
-//   candidates and the Ehrenfests' step f <- f* at those sites (Sec. 3.2;
-//   (ESLB)), so one time step is one launch.
-//   k_select         the same selection as a stand-alone kernel (test hook)
+//   k_collide_d2q9   the whole time step in one persistent launch: every
+//                    warp walks row tiles of 32 x VEC sites (pull-stream +
+//                    moments + f* + dS + LBGK), appends the sites with
+//                    dS > delta to a global candidate list (warp ballot, one
+//                    atomic per tile that has any), and the block that
+//                    finishes last runs the global radix select of the k
+//                    largest dS and the Ehrenfests' step f <- f* at those
+//                    sites (Sec. 3.2; (ESLB)).  No block waits for another.
+//   k_collide_site   the same step, one site per thread (D1Q3)
+//   k_select         the selection as a stand-alone kernel (test hook)
 #pragma once
+
+#include <algorithm>
 
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
@@ -20,66 +22,12 @@ namespace lbm {
 
 constexpr int kSelectThreads = 1024;
 constexpr int kSiteBlock = 256;      // one-site-per-thread kernels
-
-template <int N>
-struct BlockCand {
-    unsigned long long key[N];
-    unsigned idx[N];
-    unsigned count;
-    unsigned base;
-    unsigned cnt2;
-    int is_last;
-    int nsel;
-    TopkScratch sc;
-};
-
-// Append (dS, site) to the block's candidate list.
-template <int N>
-__device__ __forceinline__ void push_candidate(BlockCand<N>& sh, double ds, unsigned site) {
-    const unsigned slot = atomicAdd(&sh.count, 1u);
-    sh.key[slot] = ds_key(ds);
-    sh.idx[slot] = site;
-}
-
-// Block stage of the selection: keep at most k candidates per block (all of
-// them if there are no more than k), appended to the global candidate list.
-template <int N>
-__device__ void block_emit(const Params& P, BlockCand<N>& sh) {
-    __syncthreads();
-    const int n = (int)sh.count;
-    if (n == 0) return;
-    const int tid = threadIdx.x;
-    if (n <= P.k) {
-        if (tid == 0) sh.base = atomicAdd(P.cand_count, (unsigned)n);
-        __syncthreads();
-        for (int e = tid; e < n; e += blockDim.x) {
-            P.cand_key[sh.base + e] = sh.key[e];
-            P.cand_idx[sh.base + e] = sh.idx[e];
-        }
-        return;
-    }
-    const Thresh th = block_topk(sh.sc, n, P.k, [&](int e) { return sh.key[e]; },
-                                 [&](int e) { return sh.idx[e]; });
-    if (tid == 0) {
-        sh.base = atomicAdd(P.cand_count, (unsigned)P.k);
-        sh.cnt2 = 0;
-    }
-    __syncthreads();
-    for (int e = tid; e < n; e += blockDim.x) {
-        if (th.selected(sh.key[e], sh.idx[e])) {
-            const unsigned s = atomicAdd(&sh.cnt2, 1u);
-            if (s < (unsigned)P.k) {   // exactly k are selected; the check only bounds the write
-                P.cand_key[sh.base + s] = sh.key[e];
-                P.cand_idx[sh.base + s] = sh.idx[e];
-            }
-        }
-    }
-}
+constexpr int kStage = 1024;         // candidates staged in shared memory by the last block
 
 template <typename L, typename T, int EQ>
 __device__ __forceinline__ void equilibrium(const Params& P, T drho, T rho, T ux, T uy, T* gs) {
     if constexpr (EQ == EQ_POLY) feq_poly<L, T>(drho, rho, ux, uy, gs);
-    else feq_entropic<L, T>(rho, ux, uy, T(P.rho0), gs);
+    else feq_entropic<L, T>(rho, ux, uy, Par<T>::rho0(P), gs);
 }
 
 template <typename L, typename T>
@@ -116,7 +64,7 @@ template <typename L, typename T, int EQ>
 __device__ __forceinline__ void site_equilibrium(const Params& P, const T* g, T* gs, T& rho, T& ux,
                                                  T& uy) {
     T drho, jx, jy;
-    moments<L, T>(g, T(P.rho0), drho, rho, jx, jy);
+    moments<L, T>(g, Par<T>::rho0(P), drho, rho, jx, jy);
     velocity<T>(jx, jy, rho, ux, uy);
     equilibrium<L, T, EQ>(P, drho, rho, ux, uy, gs);
 }
@@ -134,12 +82,13 @@ __device__ __noinline__ double delta_s_fp64(PopArr<L::Q, T> g, double rho0) {
     return delta_s_exact<L, double>(gd, gs, rho0);
 }
 
-// Per-site update after the gather: moments, f*, dS, LBGK.
+// Per-site update after the gather: moments, f*, the dS bound, LBGK.
 // g: pre-collision deviations in, post-collision deviations out.
-// Returns dS (negative: cleared by the bound, not a candidate).
+// Returns true when the bound does not clear the site (dS may exceed delta):
+// its exact dS is then evaluated later from the unchanged source field.
 template <typename L, typename T, int EQ>
-__device__ __forceinline__ double update_site(const Params& P, T* g, int x, int y, long long t,
-                                              bool& nonfinite) {
+__device__ __forceinline__ bool update_site(const Params& P, T* g, int x, int y, long long t,
+                                            bool& nonfinite) {
     T gs[L::Q], rho, ux, uy;
     site_equilibrium<L, T, EQ>(P, g, gs, rho, ux, uy);
     nonfinite |= !isfinite(rho + ux + uy);
@@ -148,35 +97,76 @@ __device__ __forceinline__ double update_site(const Params& P, T* g, int x, int 
     T d[L::Q];
 #pragma unroll
     for (int i = 0; i < L::Q; i++) d[i] = g[i] - gs[i];
-    double ds = -1.0;
-    if (P.k > 0 && !ds_cleared<L, T, EQ>(d, gs, rho, ux, uy, T(P.rho0), T(P.delta))) {
-        PopArr<L::Q, T> ga, gsa;
-#pragma unroll
-        for (int i = 0; i < L::Q; i++) { ga.v[i] = g[i]; gsa.v[i] = gs[i]; }
-        ds = (double)delta_s_slow<L, T>(ga, gsa, T(P.rho0));
-        if (P.recheck && isfinite(ds) && fabs(ds - P.delta) <= 1e-3 * fabs(P.delta))
-            ds = delta_s_fp64<L, T, EQ>(ga, P.rho0);
-    }
-    const T nb2 = T(-2) * T(P.beta);
+    const bool pending =
+        P.k > 0 && !ds_cleared<L, T, EQ>(d, gs, rho, ux, uy, Par<T>::rho0(P), Par<T>::delta(P));
+    const T nb2 = T(-2) * Par<T>::beta(P);
 #pragma unroll
     for (int i = 0; i < L::Q; i++) g[i] = dfma<T>(nb2, d[i], g[i]);
+    return pending;
+}
+
+// Exact dS of site (x, y) from the source field (the pre-collision state is
+// re-gathered; the source is not written during a step).  The precision
+// form decides the sites within 1e-3 of delta in FP64; the value kept for
+// ranking then stays on the same side of delta.  Returns dS in T (NaN for a
+// non-finite state).
+template <typename L, typename S, int EQ>
+__device__ __noinline__ typename Store<S>::T resolve_ds(const Params& P, int x, int y) {
+    using T = typename Store<S>::T;
+    T g[L::Q], gs[L::Q], rho, ux, uy;
+    gather_site<L, S>(P, x, y, g);
+    site_equilibrium<L, T, EQ>(P, g, gs, rho, ux, uy);
+    T ds = delta_s_exact<L, T>(g, gs, Par<T>::rho0(P));
+    if (P.recheck && isfinite(ds) && fabs((double)ds - P.delta) <= 1e-3 * fabs(P.delta)) {
+        PopArr<L::Q, T> ga;
+#pragma unroll
+        for (int i = 0; i < L::Q; i++) ga.v[i] = g[i];
+        const double d64 = delta_s_fp64<L, T, EQ>(ga, P.rho0);
+        const T dl = Par<T>::delta(P);
+        if (d64 > P.delta) ds = (T)d64 > dl ? (T)d64 : nextafter(dl, T(INFINITY));
+        else ds = T(-1);
+    }
     return ds;
 }
 
+// Warp-level append of candidates (sites with dS > delta) to the global
+// list: one ballot, one atomic per warp when any lane has a candidate.
+// Every lane of the warp must call it.
+template <typename T>
+__device__ __forceinline__ void warp_push(const Params& P, bool cand, T ds, unsigned site) {
+    const unsigned m = __ballot_sync(0xffffffffu, cand);
+    if (m == 0) return;
+    const int lane = threadIdx.x & 31;
+    unsigned base = 0;
+    if (lane == 0) base = atomicAdd(P.cand_count, (unsigned)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (cand) {
+        const unsigned slot = base + __popc(m & ((1u << lane) - 1u));
+        P.cand_key[slot] = ds_key((double)ds);
+        P.cand_idx[slot] = site;
+    }
+}
+
 // ---------------------------------------------------------------------------
-// Global selection and Ehrenfests' step, run by one block: the last
-// stream-collide block of a step, or the stand-alone select kernel.
+// Global selection and Ehrenfests' step, run by one block: the last block of
+// a stream-collide launch, or the stand-alone select kernel.
 //   mode 0: select among the candidates (or replay a given list), overwrite
 //           the LBGK output of the selected sites with f* (Sec. 3.2; (ESLB)),
 //           log the count and advance the step counter;
 //   mode 1: select only (test hook).
-// stage_key/stage_idx: shared memory for up to stage_cap candidates (larger
-// candidate sets are ranked in place in global memory).
+// Candidates are staged in shared memory when they fit; larger sets are
+// ranked in place in global memory.
 // ---------------------------------------------------------------------------
+struct SelectShared {
+    TopkScratch sc;
+    int nsel;
+    unsigned cnt;
+};
+
 template <typename L, typename S, int EQ>
-__device__ void select_and_fix(const Params& P, TopkScratch& sc, int& nsel_sh, unsigned& cnt_sh,
-                               unsigned long long* stage_key, unsigned* stage_idx, int stage_cap,
-                               int mode) {
+__device__ __noinline__ void select_and_fix(const Params& P, SelectShared& ss,
+                                            unsigned long long* stage_key, unsigned* stage_idx,
+                                            int stage_cap, int mode) {
     using T = typename Store<S>::T;
     const int tid = threadIdx.x, nt = blockDim.x;
     const long long t = __ldcg(P.step);
@@ -186,14 +176,14 @@ __device__ void select_and_fix(const Params& P, TopkScratch& sc, int& nsel_sh, u
         const int c = P.replay_cnt[r];
         const long long off = P.replay_off[r];
         for (int j = tid; j < c; j += nt) P.sel_idx[j] = P.replay_idx[off + j];
-        if (tid == 0) nsel_sh = c;
+        if (tid == 0) ss.nsel = c;
     } else if (P.k <= 0) {
-        if (tid == 0) nsel_sh = 0;
+        if (tid == 0) ss.nsel = 0;
     } else {
         const int n = (int)__ldcg(P.cand_count);
         if (n <= P.k) {
             for (int j = tid; j < n; j += nt) P.sel_idx[j] = (int)__ldcg(P.cand_idx + j);
-            if (tid == 0) nsel_sh = n;
+            if (tid == 0) ss.nsel = n;
         } else {
             const bool staged = n <= stage_cap;
             if (staged) {
@@ -205,21 +195,21 @@ __device__ void select_and_fix(const Params& P, TopkScratch& sc, int& nsel_sh, u
             }
             auto keyat = [&](int e) { return staged ? stage_key[e] : __ldcg(P.cand_key + e); };
             auto idat = [&](int e) { return staged ? stage_idx[e] : __ldcg(P.cand_idx + e); };
-            const Thresh th = block_topk(sc, n, P.k, keyat, idat);
-            if (tid == 0) cnt_sh = 0;
+            const Thresh th = block_topk(ss.sc, n, P.k, keyat, idat);
+            if (tid == 0) ss.cnt = 0;
             __syncthreads();
             for (int j = tid; j < n; j += nt) {
                 const unsigned id = idat(j);
                 if (th.selected(keyat(j), id)) {
-                    const unsigned s = atomicAdd(&cnt_sh, 1u);
-                    if (s < (unsigned)P.k) P.sel_idx[s] = (int)id;
+                    const unsigned s = atomicAdd(&ss.cnt, 1u);
+                    if (s < (unsigned)P.k) P.sel_idx[s] = (int)id;   // exactly k; bounds the write
                 }
             }
-            if (tid == 0) nsel_sh = P.k;
+            if (tid == 0) ss.nsel = P.k;
         }
     }
     __syncthreads();
-    const int m = nsel_sh;
+    const int m = ss.nsel;
     if (mode == 0) {
         const long long nsites = (long long)P.nx * P.ny;
         for (int j = tid; j < m; j += nt) {
@@ -246,11 +236,59 @@ __device__ void select_and_fix(const Params& P, TopkScratch& sc, int& nsel_sh, u
     }
 }
 
-// End of a stream-collide block: publish this block's writes, take a ticket;
-// the block that takes the last ticket runs the global selection and the
+// End of a stream-collide block: resolve the block's pending sites (exact
+// dS, candidates appended), publish the block's writes, take a ticket; the
+// block that takes the last ticket first resolves the pending sites that did
+// not fit in any block's list, then runs the global selection and the
 // Ehrenfests' step for the whole grid.  No block ever waits for another.
-template <typename L, typename S, int EQ, int N>
-__device__ __forceinline__ void finish_block(const Params& P, BlockCand<N>& sh) {
+constexpr int kPend = 2048;   // pending sites kept per block in shared memory
+
+struct FinishShared {
+    SelectShared ss;
+    unsigned long long key[kStage];
+    unsigned idx[kStage];
+    unsigned pend[kPend];
+    unsigned npend;
+    int is_last;
+};
+
+// Warp-level append of pending sites to the block list (overflow: global).
+__device__ __forceinline__ void warp_pend(const Params& P, FinishShared& fs, bool pend, unsigned site) {
+    const unsigned m = __ballot_sync(0xffffffffu, pend);
+    if (m == 0) return;
+    const int lane = threadIdx.x & 31;
+    unsigned base = 0;
+    if (lane == 0) base = atomicAdd(&fs.npend, (unsigned)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (pend) {
+        const unsigned slot = base + __popc(m & ((1u << lane) - 1u));
+        if (slot < (unsigned)kPend) fs.pend[slot] = site;
+        else P.pend_idx[atomicAdd(P.pend_count, 1u)] = site;
+    }
+}
+
+// Exact dS of n pending sites, appending the candidates; all threads call.
+template <typename L, typename S, int EQ, typename SiteAt>
+__device__ void resolve_list(const Params& P, int n, SiteAt site_at) {
+    using T = typename Store<S>::T;
+    const T delta = Par<T>::delta(P);
+    for (int b = 0; b < n; b += blockDim.x) {
+        const int j = b + (int)threadIdx.x;
+        unsigned site = 0;
+        T ds = T(-1);
+        if (j < n) {
+            site = site_at(j);
+            ds = resolve_ds<L, S, EQ>(P, (int)(site % (unsigned)P.nx), (int)(site / (unsigned)P.nx));
+        }
+        warp_push<T>(P, ds > delta, ds, site);
+    }
+}
+
+template <typename L, typename S, int EQ>
+__device__ __forceinline__ void finish_block(const Params& P, FinishShared& fs) {
+    __syncthreads();
+    const int np = (int)min(fs.npend, (unsigned)kPend);
+    if (np > 0) resolve_list<L, S, EQ>(P, np, [&](int j) { return fs.pend[j]; });
     // the barrier makes the block's writes visible to thread 0, whose
     // device-scope fence then orders all of them before the ticket
     __syncthreads();
@@ -259,19 +297,56 @@ __device__ __forceinline__ void finish_block(const Params& P, BlockCand<N>& sh) 
         const unsigned nb = gridDim.x * gridDim.y;
         const unsigned tk = atomicAdd(P.ticket, 1u);
         __threadfence();
-        sh.is_last = (tk == nb - 1);
+        fs.is_last = (tk == nb - 1);
     }
     __syncthreads();
-    if (sh.is_last) {
-        select_and_fix<L, S, EQ>(P, sh.sc, sh.nsel, sh.cnt2, sh.key, sh.idx, N, 0);
+    if (fs.is_last) {
+        const int ng = (int)__ldcg(P.pend_count);
+        if (ng > 0) {
+            resolve_list<L, S, EQ>(P, ng, [&](int j) { return __ldcg(P.pend_idx + j); });
+            __syncthreads();
+            if (threadIdx.x == 0) *P.pend_count = 0;
+        }
+        __threadfence_block();
+        select_and_fix<L, S, EQ>(P, fs.ss, fs.key, fs.idx, kStage, 0);
         if (threadIdx.x == 0) *P.ticket = 0;
     }
+}
+
+// Boundary site (or any site of the first step after a state upload): gather
+// with the boundary rules, update, store.  Returns bit 0: non-finite,
+// bit 1: pending.
+template <typename S, int EQ>
+__device__ __noinline__ int boundary_site(const Params& P, int x, int y, long long t) {
+    using L = D2Q9;
+    using T = typename Store<S>::T;
+    const long long o = (long long)y * P.nxp + x;
+    T g[L::Q];
+    bool nonfinite = false, pending = false;
+    if (is_solid(P, x, y)) {
+#pragma unroll
+        for (int i = 0; i < L::Q; i++) g[i] = T(0);
+    } else {
+        gather_site<L, S>(P, x, y, g);
+        pending = update_site<L, T, EQ>(P, g, x, y, t, nonfinite);
+    }
+#pragma unroll
+    for (int i = 0; i < L::Q; i++) Store<S>::store(P.dst, i * P.plane + o, g[i]);
+    return (nonfinite ? 1 : 0) | (pending ? 2 : 0);
 }
 
 // ---------------------------------------------------------------------------
 // Vector loads and stores of VEC consecutive populations (aligned).
 // ---------------------------------------------------------------------------
 template <typename S, int VEC> struct VecIO;
+template <typename S> struct VecIO<S, 1> {
+    __device__ static void load(const void* p, long long i, typename Store<S>::T* v) {
+        v[0] = Store<S>::load(p, i);
+    }
+    __device__ static void store(void* p, long long i, const typename Store<S>::T* v) {
+        Store<S>::store(p, i, v[0]);
+    }
+};
 template <> struct VecIO<float, 4> {
     __device__ static void load(const void* p, long long i, float* v) {
         const float4 a = __ldg(reinterpret_cast<const float4*>(static_cast<const float*>(p) + i));
@@ -339,170 +414,169 @@ template <> struct VecIO<__half, 2> {
     }
 };
 
-template <typename S> struct VecIO<S, 1> {
-    __device__ static void load(const void* p, long long i, typename Store<S>::T* v) {
-        v[0] = Store<S>::load(p, i);
-    }
-    __device__ static void store(void* p, long long i, const typename Store<S>::T* v) {
-        Store<S>::store(p, i, v[0]);
-    }
-};
+// Interior-path accessors with 32-bit element indices (every population
+// array holds fewer than 2^31 elements; checked at creation).
+template <typename S, int VEC>
+__device__ __forceinline__ void load_vec(const S* __restrict__ p, int i, typename Store<S>::T* v) {
+    VecIO<S, VEC>::load(p + i, 0, v);
+}
+template <typename S, int VEC>
+__device__ __forceinline__ void store_vec(S* __restrict__ p, int i, const typename Store<S>::T* v) {
+    VecIO<S, VEC>::store(p + i, 0, v);
+}
 
-// A tile [x0, x0 + TX) x [y0, y0 + TY) is interior when every site of the
-// tile and of its one-site halo is fluid and inside the grid: its gather is
-// then a pure shift with no boundary rule.
-template <int TX, int TY>
-__device__ __forceinline__ bool tile_interior(const Params& P, int x0, int y0) {
-    if (x0 < 1 || x0 + TX > P.nx - 1 || y0 < 1 || y0 + TY > P.ny - 1) return false;
+// A row tile [x0, x0 + TX) of row y is interior when the tile and its
+// one-site halo are fluid and inside the grid: its gather is a pure shift.
+template <int TX>
+__device__ __forceinline__ bool tile_interior(const Params& P, int x0, int y) {
+    if (x0 < 1 || x0 + TX > P.nx - 1 || y < 1 || y > P.ny - 2) return false;
     if (P.ow > 0) {
         const bool apart = (x0 + TX + 1 <= P.ox0) || (x0 - 1 >= P.ox0 + P.ow) ||
-                           (y0 + TY + 1 <= P.oy0) || (y0 - 1 >= P.oy0 + P.oh);
+                           (y + 2 <= P.oy0) || (y - 1 >= P.oy0 + P.oh);
         if (!apart) return false;
     }
     return true;
 }
 
 // ---------------------------------------------------------------------------
-// K1 for D2Q9: one warp per row segment of 32 * VEC sites, ROWS rows per
-// block.  Interior tiles: aligned VEC-wide loads per population plane, the
-// x-shifted planes completed by one warp shuffle and one halo load per warp.
-// Boundary tiles (and the first step after a state upload): per-site gather.
+// K1 for D2Q9, persistent: the grid holds as many blocks as fit on the
+// GPU at once; each block processes a contiguous range of row tiles of
+// 32 x VEC consecutive sites, its warps taking the range's tiles in turn.
+// Interior tiles: aligned VEC-wide loads per population plane, the
+// x-shifted planes completed by one warp shuffle and one halo load.
+// Boundary tiles (and the first step after a state upload): per-site gather
+// with the boundary rules.
 // ---------------------------------------------------------------------------
-template <typename S, int EQ, int VEC, int ROWS, int MINB>
-__global__ void __launch_bounds__(32 * ROWS, MINB) k_collide_d2q9(Params P) {
+template <typename S, int EQ, int VEC, int WARPS, int MINB>
+__global__ void __launch_bounds__(32 * WARPS, MINB) k_collide_d2q9(const __grid_constant__ Params P) {
     using L = D2Q9;
     using T = typename Store<S>::T;
     constexpr int TX = 32 * VEC;
-    constexpr int NS = 32 * ROWS * VEC;
-    __shared__ BlockCand<NS> sh;
+    __shared__ FinishShared fs;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * ROWS;
-    const int y = y0 + warp, xs = x0 + lane * VEC;
-    if (threadIdx.x == 0) sh.count = 0;
+    if (threadIdx.x == 0) fs.npend = 0;
     __syncthreads();
     const long long t = *P.step;
+    const S* __restrict__ src = static_cast<const S*>(P.src);
+    S* __restrict__ dst = static_cast<S*>(P.dst);
+    const int nxp = P.nxp, plane = (int)P.plane;
+    // Each block owns a contiguous range of row tiles (row-major); its warps
+    // take the range's tiles in turn.  Boundary tiles, which cost more, are
+    // then spread evenly over blocks.
+    const int tiles_x = (P.nx + TX - 1) / TX;
+    const int tiles = tiles_x * P.ny;
+    const int per_block = (tiles + gridDim.x - 1) / gridDim.x;
+    const int t0 = blockIdx.x * per_block;
+    const int t1 = min(t0 + per_block, tiles);
+    int w = t0 + warp;
+    int y = w / tiles_x, xt = w - y * tiles_x;
     bool nonfinite = false;
-    if (!P.prestream && tile_interior<TX, ROWS>(P, x0, y0)) {
-        T g[VEC][L::Q];
+    for (; w < t1; w += WARPS) {
+        const int x0 = xt * TX;
+        const int xs = x0 + lane * VEC;
+        if (!P.prestream && tile_interior<TX>(P, x0, y)) {
+            const int row = y * nxp + xs;
+            T g[VEC][L::Q];
 #pragma unroll
-        for (int i = 0; i < L::Q; i++) {
-            const long long row = i * P.plane + (long long)(y - L::cy(i)) * P.nxp;
-            T v[VEC];
-            VecIO<S, VEC>::load(P.src, row + xs, v);
-            if (L::cx(i) == 0) {
+            for (int i = 0; i < L::Q; i++) {
+                const int at = i * plane + row - L::cy(i) * nxp;
+                T v[VEC];
+                load_vec<S, VEC>(src, at, v);
+                if (L::cx(i) == 0) {
 #pragma unroll
-                for (int s = 0; s < VEC; s++) g[s][i] = v[s];
-            } else if (L::cx(i) == 1) {
-                // source x - 1: the previous lane's last element
-                T prev = __shfl_up_sync(0xffffffffu, v[VEC - 1], 1);
-                if (lane == 0) prev = Store<S>::load(P.src, row + xs - 1);
-                g[0][i] = prev;
+                    for (int s = 0; s < VEC; s++) g[s][i] = v[s];
+                } else if (L::cx(i) == 1) {
+                    // source x - 1: the previous lane's last element
+                    T prev = __shfl_up_sync(0xffffffffu, v[VEC - 1], 1);
+                    if (lane == 0) prev = Store<S>::load(src + at - 1, 0);
+                    g[0][i] = prev;
 #pragma unroll
-                for (int s = 1; s < VEC; s++) g[s][i] = v[s - 1];
-            } else {
-                // source x + 1: the next lane's first element
-                T next = __shfl_down_sync(0xffffffffu, v[0], 1);
-                if (lane == 31) next = Store<S>::load(P.src, row + xs + VEC);
+                    for (int s = 1; s < VEC; s++) g[s][i] = v[s - 1];
+                } else {
+                    // source x + 1: the next lane's first element
+                    T next = __shfl_down_sync(0xffffffffu, v[0], 1);
+                    if (lane == 31) next = Store<S>::load(src + at + VEC, 0);
 #pragma unroll
-                for (int s = 0; s < VEC - 1; s++) g[s][i] = v[s + 1];
-                g[VEC - 1][i] = next;
+                    for (int s = 0; s < VEC - 1; s++) g[s][i] = v[s + 1];
+                    g[VEC - 1][i] = next;
+                }
             }
-        }
+            bool pend[VEC];
 #pragma unroll
-        for (int s = 0; s < VEC; s++) {
-            const int x = xs + s;
-            const double ds = update_site<L, T, EQ>(P, g[s], x, y, t, nonfinite);
-            if (ds > P.delta) push_candidate(sh, ds, (unsigned)(y * P.nx + x));
-        }
-        const long long base = (long long)y * P.nxp + xs;
+            for (int s = 0; s < VEC; s++) pend[s] = update_site<L, T, EQ>(P, g[s], xs + s, y, t, nonfinite);
 #pragma unroll
-        for (int i = 0; i < L::Q; i++) {
-            T v[VEC];
+            for (int i = 0; i < L::Q; i++) {
+                T v[VEC];
 #pragma unroll
-            for (int s = 0; s < VEC; s++) v[s] = g[s][i];
-            VecIO<S, VEC>::store(P.dst, i * P.plane + base, v);
-        }
-    } else {
-        // boundary tile (or the first step after a state upload): one site at
-        // a time with the boundary rules
+                for (int s = 0; s < VEC; s++) v[s] = g[s][i];
+                store_vec<S, VEC>(dst, i * plane + row, v);
+            }
+#pragma unroll
+            for (int s = 0; s < VEC; s++) warp_pend(P, fs, pend[s], (unsigned)(y * P.nx + xs + s));
+        } else {
 #pragma unroll 1
-        for (int s = 0; s < VEC; s++) {
-            const int x = xs + s;
-            if (x >= P.nx || y >= P.ny) continue;
-            const long long o = (long long)y * P.nxp + x;
-            T g[L::Q];
-            if (is_solid(P, x, y)) {
-#pragma unroll
-                for (int i = 0; i < L::Q; i++) g[i] = T(0);
-            } else {
-                gather_site<L, S>(P, x, y, g);
-                const double ds = update_site<L, T, EQ>(P, g, x, y, t, nonfinite);
-                if (ds > P.delta) push_candidate(sh, ds, (unsigned)(y * P.nx + x));
+            for (int s = 0; s < VEC; s++) {
+                const int x = xs + s;
+                int r = 0;
+                if (x < P.nx) r = boundary_site<S, EQ>(P, x, y, t);
+                nonfinite |= (r & 1) != 0;
+                warp_pend(P, fs, (r & 2) != 0, (unsigned)(y * P.nx + x));
             }
-#pragma unroll
-            for (int i = 0; i < L::Q; i++) Store<S>::store(P.dst, i * P.plane + o, g[i]);
         }
+        xt += WARPS;
+        while (xt >= tiles_x) { xt -= tiles_x; y++; }
     }
     if (nonfinite) atomicOr(P.err, ERR_NONFINITE);
-    if (P.k > 0) block_emit(P, sh);
-    finish_block<L, S, EQ>(P, sh);
+    finish_block<L, S, EQ>(P, fs);
 }
 
 // ---------------------------------------------------------------------------
 // K1, one site per thread (D1Q3).
 // ---------------------------------------------------------------------------
 template <typename L, typename S, int EQ>
-__global__ void __launch_bounds__(kSiteBlock) k_collide_site(Params P) {
+__global__ void __launch_bounds__(kSiteBlock) k_collide_site(const __grid_constant__ Params P) {
     using T = typename Store<S>::T;
-    __shared__ BlockCand<kSiteBlock> sh;
-    if (threadIdx.x == 0) sh.count = 0;
+    __shared__ FinishShared fs;
+    if (threadIdx.x == 0) fs.npend = 0;
+    __syncthreads();
     const long long t = *P.step;
     const long long sid = (long long)blockIdx.x * kSiteBlock + threadIdx.x;
     const int x = (int)(sid % P.nx), y = (int)(sid / P.nx);
     const bool inside = sid < (long long)P.nx * P.ny;
     const bool valid = inside && !is_solid(P, x, y);
-    bool nonfinite = false;
+    bool nonfinite = false, pending = false;
     T g[L::Q];
-    if (valid) gather_site<L, S>(P, x, y, g);
-    __syncthreads();
     if (valid) {
-        const double ds = update_site<L, T, EQ>(P, g, x, y, t, nonfinite);
-        if (ds > P.delta) push_candidate(sh, ds, (unsigned)sid);
+        gather_site<L, S>(P, x, y, g);
+        pending = update_site<L, T, EQ>(P, g, x, y, t, nonfinite);
     }
     if (inside) {
         const long long o = (long long)y * P.nxp + x;
 #pragma unroll
         for (int i = 0; i < L::Q; i++) Store<S>::store(P.dst, i * P.plane + o, valid ? g[i] : T(0));
     }
+    warp_pend(P, fs, pending, (unsigned)sid);
     if (nonfinite) atomicOr(P.err, ERR_NONFINITE);
-    if (P.k > 0) block_emit(P, sh);
-    finish_block<L, S, EQ>(P, sh);
+    finish_block<L, S, EQ>(P, fs);
 }
 
 // Stand-alone selection (select-only test hook).
 template <typename L, typename S, int EQ>
-__global__ void __launch_bounds__(kSelectThreads) k_select(Params P, int stage_cap, int mode) {
+__global__ void __launch_bounds__(kSelectThreads) k_select(const __grid_constant__ Params P, int stage_cap,
+                                                           int mode) {
     extern __shared__ unsigned long long dyn[];
-    __shared__ TopkScratch sc;
-    __shared__ int nsel;
-    __shared__ unsigned cnt;
-    select_and_fix<L, S, EQ>(P, sc, nsel, cnt, dyn, reinterpret_cast<unsigned*>(dyn + stage_cap),
-                             stage_cap, mode);
+    __shared__ SelectShared ss;
+    select_and_fix<L, S, EQ>(P, ss, dyn, reinterpret_cast<unsigned*>(dyn + stage_cap), stage_cap, mode);
 }
 
 #ifdef LBM_DEFINE_EMIT_FROM_DS
-// Candidates from a given dS array (select-only test hook): the same block
-// stage as K1, 1024 values per block.
-__global__ void __launch_bounds__(256) k_emit_from_ds(Params P, const double* ds, int n) {
-    __shared__ BlockCand<1024> sh;
-    if (threadIdx.x == 0) sh.count = 0;
-    __syncthreads();
-    const long long b = (long long)blockIdx.x * 1024;
-    for (int s = threadIdx.x; s < 1024; s += 256) {
-        const long long i = b + s;
-        if (i < n && ds[i] > P.delta) push_candidate(sh, ds[i], (unsigned)i);
-    }
-    if (P.k > 0) block_emit(P, sh);
+// Candidates from a given dS array (select-only test hook): the same warp
+// append as K1.
+__global__ void __launch_bounds__(256) k_emit_from_ds(const __grid_constant__ Params P, const double* ds,
+                                                      int n) {
+    const long long i = (long long)blockIdx.x * 256 + threadIdx.x;
+    const double v = i < n ? ds[i] : -INFINITY;
+    if (P.k > 0) warp_push<double>(P, i < n && v > P.delta, v, (unsigned)i);
 }
 #endif
 
@@ -512,7 +586,8 @@ __global__ void __launch_bounds__(256) k_emit_from_ds(Params P, const double* ds
 
 // Quasiequilibrium of given (rho, u) at every fluid site; zero elsewhere.
 template <typename L, typename S, int EQ>
-__global__ void k_init_eq(Params P, const double* rho, const double* ux, const double* uy) {
+__global__ void k_init_eq(const __grid_constant__ Params P, const double* rho, const double* ux,
+                          const double* uy) {
     using T = typename Store<S>::T;
     const long long sid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (sid >= (long long)P.nx * P.ny) return;
@@ -524,7 +599,7 @@ __global__ void k_init_eq(Params P, const double* rho, const double* ux, const d
         for (int i = 0; i < L::Q; i++) gs[i] = T(0);
     } else {
         const T r = T(rho[sid]), u = T(ux[sid]), v = uy ? T(uy[sid]) : T(0);
-        equilibrium<L, T, EQ>(P, r - T(P.rho0), r, u, v, gs);
+        equilibrium<L, T, EQ>(P, r - Par<T>::rho0(P), r, u, v, gs);
     }
 #pragma unroll
     for (int i = 0; i < L::Q; i++) Store<S>::store(P.dst, i * P.plane + o, gs[i]);
@@ -532,7 +607,7 @@ __global__ void k_init_eq(Params P, const double* rho, const double* ux, const d
 
 // FP64 populations [Q][ny][nx] -> deviation storage.
 template <typename L, typename S>
-__global__ void k_import(Params P, const double* f) {
+__global__ void k_import(const __grid_constant__ Params P, const double* f) {
     const long long N = (long long)P.nx * P.ny;
     const long long sid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (sid >= N) return;
@@ -549,7 +624,8 @@ __global__ void k_import(Params P, const double* f) {
 // Pre-collision state of the current step (gather of src), exported as
 // mode 0: populations f [Q][ny][nx]; 1: rho, ux, uy, 2E; 2: exact dS.
 template <typename L, typename S, int EQ>
-__global__ void k_export(Params P, int mode, double* o0, double* o1, double* o2, double* o3) {
+__global__ void k_export(const __grid_constant__ Params P, int mode, double* o0, double* o1, double* o2,
+                         double* o3) {
     using T = typename Store<S>::T;
     const long long N = (long long)P.nx * P.ny;
     const long long sid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -588,21 +664,31 @@ __global__ void k_export(Params P, int mode, double* o0, double* o1, double* o2,
     } else {
         T gs[L::Q], rho, ux, uy;
         site_equilibrium<L, T, EQ>(P, g, gs, rho, ux, uy);
-        o0[sid] = (double)delta_s_exact<L, T>(g, gs, T(P.rho0));
+        o0[sid] = (double)delta_s_exact<L, T>(g, gs, Par<T>::rho0(P));
     }
 }
 
 // ---------------------------------------------------------------------------
 // Launchers for one storage type.  Tile shapes of the D2Q9 kernel (sites per
-// thread in x, rows per block = warps, minimum resident blocks per SM):
-//   0: 1 x 8, 3     1: 1 x 8, 4     2: 2 x 8, 2     3: 4 x 8, 1
+// thread in x, warps per block, minimum resident blocks per SM):
+//   0: 1, 8, 3     1: 1, 8, 4     2: 2, 8, 2     3: 4, 8, 1
+// The persistent grid is (resident blocks per SM) x (SM count), from the
+// occupancy calculator, capped by the number of row tiles.
 // ---------------------------------------------------------------------------
-
-template <typename S, int EQ, int VEC, int ROWS, int MINB>
+template <typename S, int EQ, int VEC, int WARPS, int MINB>
 cudaError_t launch_d2q9(const Params& P, cudaStream_t st) {
-    dim3 grid((P.nx + 32 * VEC - 1) / (32 * VEC), (P.ny + ROWS - 1) / ROWS);
-    k_collide_d2q9<S, EQ, VEC, ROWS, MINB><<<grid, 32 * ROWS, 0, st>>>(P);
+    const long long tiles = (long long)((P.nx + 32 * VEC - 1) / (32 * VEC)) * P.ny;
+    const long long want = (tiles + 4 * WARPS - 1) / (4 * WARPS);   // at least 4 tiles per warp
+    const unsigned blocks = (unsigned)std::max(1ll, std::min(want, (long long)P.grid_blocks));
+    k_collide_d2q9<S, EQ, VEC, WARPS, MINB><<<blocks, 32 * WARPS, 0, st>>>(P);
     return cudaGetLastError();
+}
+
+// Resident blocks per SM of a D2Q9 tile shape (occupancy calculator).
+template <typename S, int EQ, int VEC, int WARPS, int MINB>
+cudaError_t occupancy_d2q9(int* per_sm) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_collide_d2q9<S, EQ, VEC, WARPS, MINB>,
+                                                         32 * WARPS, 0);
 }
 
 template <typename L, typename S, int EQ>
@@ -621,6 +707,18 @@ struct LaunchImpl {
             k_collide_site<L, S, EQ><<<blocks, kSiteBlock, 0, st>>>(P);
             return cudaGetLastError();
         }
+    }
+    static cudaError_t occupancy(int shape, int* per_sm) {
+        *per_sm = 1;
+        if constexpr (L::Q == 9) {
+            switch (shape) {
+                case 1: return occupancy_d2q9<S, EQ, 1, 8, 4>(per_sm);
+                case 2: return occupancy_d2q9<S, EQ, 2, 8, 2>(per_sm);
+                case 3: return occupancy_d2q9<S, EQ, 4, 8, 1>(per_sm);
+                default: return occupancy_d2q9<S, EQ, 1, 8, 3>(per_sm);
+            }
+        }
+        return cudaSuccess;
     }
     static cudaError_t select(const Params& P, int stage_cap, int mode, cudaStream_t st) {
         const size_t smem = (size_t)stage_cap * (sizeof(unsigned long long) + sizeof(unsigned));
@@ -657,6 +755,7 @@ struct LaunchImpl {
         l.import_state = &import_state;
         l.export_state = &export_state;
         l.set_smem = &set_smem;
+        l.occupancy = &occupancy;
         return l;
     }
 };

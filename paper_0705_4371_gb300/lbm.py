@@ -259,9 +259,10 @@ class Lattice:
         _check(self.L.lb_set_tile_shape(self.h, int(shape)))
 
     def info(self):
-        out = np.zeros(5, np.int64)
+        out = np.zeros(8, np.int64)
         beta = C.c_double(0)
         _check(self.L.lb_info(self.h, _ptr(out), C.byref(beta)))
         return {"Q": int(out[0]), "nxp": int(out[1]), "bytes_per_pop": int(out[2]),
                 "bytes_per_site": int(out[3]), "launches_per_step": int(out[4]),
-                "beta": beta.value}
+                "grid_blocks": int(out[5]), "blocks_per_sm": int(out[6]),
+                "tile_shape": int(out[7]), "beta": beta.value}
