@@ -175,6 +175,34 @@ int lb_delta_s(lb_handle* h, double* ds, int on_device);
  * Runs on an internal stream and synchronises. */
 int lb_select_only(const double* ds, int n, double delta, int k, int* idx_out, int* count);
 
+/* Largest n accepted by lb_select_only_noalloc. */
+#define LB_NOALLOC_MAX_N 262144
+
+/* lb_select_only_noalloc -- the paper has no counterpart to this entry point;
+ * it exists for callers that cannot allocate device memory (code running
+ * while a stream is captured, real-time loops that must not take
+ * cudaMalloc's implicit device synchronisation, hosts that manage all device
+ * memory themselves).  It makes the same selection as lb_select_only: among
+ * ds[0..n) the k largest values > delta (all of them if fewer qualify), ties
+ * to the lower index, through the same kernels.
+ *   ds:      DEVICE pointer to n FP64 values (read);
+ *   idx_out: DEVICE pointer to min(n, k) ints (written; order unspecified);
+ *   count:   DEVICE pointer to one int (written: the number selected);
+ *   cuda_stream: the stream the work is queued on (NULL: the legacy default
+ *            stream).  The call is asynchronous: the outputs are valid once
+ *            the stream has reached this work.
+ * It calls no cudaMalloc, cudaFree or other allocating routine.  Its working
+ * memory is one fixed device array of about 3 MB per GPU (room for
+ * LB_NOALLOC_MAX_N candidates), held by every GPU that loads the library
+ * until the process exits; n > LB_NOALLOC_MAX_N is rejected with LB_ERR_ARG.
+ * The first call on a device looks up that array's device address (and sets
+ * the select kernel's shared-memory limit) with that device current; make
+ * that first call before any stream capture.  All calls share the array:
+ * calls that overlap on the GPU (different streams, or different host
+ * threads, without ordering between them) race and give wrong results. */
+int lb_select_only_noalloc(const double* ds, int n, double delta, int k, int* idx_out, int* count,
+                           void* cuda_stream);
+
 /* Test hook: for the next nsteps steps, use the given selections instead of
  * selecting (replay of another implementation's choices).  counts[t] sites
  * for step t, their indices concatenated in idx.  Host arrays. */

@@ -47,6 +47,8 @@ size_t storage_bytes(int prec) { return prec == LB_F64 ? 8 : (prec == LB_F16_DEV
 
 }  // namespace
 
+void lbm::set_last_error(const char* msg) { g_last_error = msg; }
+
 struct lb_handle {
     int lattice, Q, nx, ny, nxp, eq, prec, k;
     double nu, beta, delta, rho0;

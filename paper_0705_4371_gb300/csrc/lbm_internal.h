@@ -27,6 +27,9 @@ Launchers launchers_f16(int lattice, int eq);
 
 constexpr int kTileShapes = 4;   // tile shapes of the D2Q9 stream-collide kernel
 
+// message returned by lb_last_error on this thread
+void set_last_error(const char* msg);
+
 // select-only test hook: candidates from a device dS array
 cudaError_t launch_emit_from_ds(const Params& P, const double* ds, int n, cudaStream_t st);
 

@@ -75,6 +75,7 @@ def load(path=None):
         "lb_kernel_times": ([H, vp, vp, vp, vp, ip], ip),
         "lb_info": ([H, vp, vp], ip),
         "lb_set_tile_shape": ([H, ip], ip),
+        "lb_select_only_noalloc": ([vp, ip, dp, ip, vp, vp, vp], ip),
         "lb_last_error": ([], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -124,6 +125,18 @@ def select_only(ds, delta, k):
     cnt = C.c_int(0)
     _check(L.lb_select_only(_ptr(ds), ds.size, float(delta), int(k), _ptr(out), C.byref(cnt)))
     return np.sort(out[:cnt.value].astype(np.int64))
+
+
+NOALLOC_MAX_N = 262144
+
+
+def select_only_noalloc(ds_ptr, n, delta, k, idx_ptr, count_ptr, stream=None):
+    """lb_select_only_noalloc on device pointers (integers); asynchronous on
+    `stream` (a cudaStream_t as an integer, or None).  Allocates nothing."""
+    L = load()
+    _check(L.lb_select_only_noalloc(C.c_void_p(ds_ptr), int(n), float(delta), int(k),
+                                    C.c_void_p(idx_ptr), C.c_void_p(count_ptr),
+                                    C.c_void_p(stream) if stream else None))
 
 
 def mlp_param_count():

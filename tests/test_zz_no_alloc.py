@@ -1,0 +1,69 @@
+"""lb_select_only_noalloc: the selection entry point for callers that cannot
+allocate device memory (stream capture in progress, real-time loops that must
+not take cudaMalloc's implicit synchronisation, hosts that own all device
+memory).  Its working memory is a fixed array inside the library, so the test
+checks that two calls in a row, which reuse that array, each give exactly the
+selection of the allocating entry point lb_select_only on the same values.
+
+This file is collected last so that a run stopping at the first failure has
+already run every other test.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from paper_0705_4371_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    from paper_0705_4371_gb300 import lbm
+    lbm.load()
+    assert torch.cuda.is_available()
+    return torch, lbm
+
+
+def _noalloc_select(torch, lbm, ds_host, delta, k):
+    dev = torch.device("cuda", 0)
+    ds = torch.from_numpy(np.ascontiguousarray(ds_host, np.float64)).to(dev)
+    out = torch.full((max(1, min(k, ds.numel())),), -1, dtype=torch.int32, device=dev)
+    cnt = torch.full((1,), -1, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    lbm.select_only_noalloc(ds.data_ptr(), ds.numel(), delta, k, out.data_ptr(), cnt.data_ptr(),
+                            stream.cuda_stream)
+    torch.cuda.synchronize(dev)
+    c = int(cnt.item())
+    return np.sort(out[:c].cpu().numpy().astype(np.int64))
+
+
+def test_two_calls_in_a_row_match_the_allocating_entry_point(env):
+    torch, lbm = env
+    cases = [
+        # (seed, n, k, ties, frac_inf, delta quantile)
+        (3001, 200000, 64, 5000, 0.01, 0.7),    # candidates beyond shared-memory staging
+        (3002, 4096, 16, 100, 0.0, 0.9),        # fewer, smaller; the array holds the old data
+    ]
+    for seed, n, k, ties, finf, q in cases:
+        ds = inputs.random_ds_with_ties(seed, n, n_ties=ties, frac_inf=finf)
+        delta = float(np.quantile(ds[np.isfinite(ds)], q))
+        got = _noalloc_select(torch, lbm, ds, delta, k)
+        ref = lbm.select_only(ds, delta, k)
+        assert got.size == min(k, int((ds > delta).sum()))
+        assert np.array_equal(got, ref)
+
+
+def test_rejects_sizes_beyond_the_fixed_memory(env):
+    torch, lbm = env
+    dev = torch.device("cuda", 0)
+    ds = torch.zeros(4, dtype=torch.float64, device=dev)
+    out = torch.zeros(4, dtype=torch.int32, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+    with pytest.raises(lbm.LBError) as e:
+        lbm.select_only_noalloc(ds.data_ptr(), lbm.NOALLOC_MAX_N + 1, 0.0, 4, out.data_ptr(),
+                                cnt.data_ptr())
+    assert e.value.code == lbm.LB_ERR_ARG
+    assert "exceeds" in str(e.value)
