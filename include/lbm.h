@@ -231,9 +231,13 @@ int lb_set_timing(lb_handle* h, int enable);
 int lb_kernel_times(lb_handle* h, double* collide_ms, long long* collide_launches,
                     double* select_ms, long long* select_launches, int reset);
 
-/* Tile shape of the D2Q9 stream-collide kernel (sites per thread in x,
- * warps per block, minimum resident blocks per SM): 0 = 1, 8, 3;
- * 1 = 1, 8, 4 (default);  2 = 2, 8, 2;  3 = 4, 8, 1.
+/* Tile shape of the D2Q9 stream-collide kernel.  Register-fed shapes (sites
+ * per thread in x, warps per block, minimum resident blocks per SM):
+ * 0 = 1, 8, 3;  1 = 1, 8, 4;  2 = 2, 8, 2;  3 = 4, 8, 1.
+ * Shared-memory-staged shapes (tensor-memory-accelerator copies of the
+ * R x 128-site block tile of every population plane plus one halo row and
+ * 16 bytes of halo columns; R rows, STAGES tiles in flight per block):
+ * 4 = R 8, STAGES 2 (default);  5 = R 4, STAGES 3.
  * Results do not depend on the shape; only the speed does (the batched
  * runner's autotuner picks it per grid). */
 int lb_set_tile_shape(lb_handle* h, int shape);

@@ -10,6 +10,9 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "../../include/lbm.h"
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
@@ -41,7 +44,7 @@ int fail(int code, const char* fmt, ...) {
 constexpr int kStageCap = 8192;      // candidates staged in shared memory by the select kernel
 constexpr int kGraphSteps = 32;      // steps per captured graph (even: buffers return)
 constexpr int kDefaultLog = 65536;
-constexpr int kDefaultTileShape = 1;  // fastest measured on GB300 for FP32 / FP16 storage
+constexpr int kDefaultTileShape = 4;  // fastest measured on GB300 (staged tiles, 2 in flight)
 
 size_t storage_bytes(int prec) { return prec == LB_F64 ? 8 : (prec == LB_F16_DEV ? 2 : 4); }
 
@@ -104,6 +107,9 @@ struct lb_handle {
     unsigned* pend_idx;
     unsigned* pend_count;
     int grid_blocks, sm_count, blocks_per_sm;
+    // tensor maps of the two population buffers (shared-memory-staged shapes)
+    CUtensorMap tmap[2];
+    unsigned* tile_counter;
 };
 
 namespace {
@@ -138,6 +144,7 @@ Params make_params(const lb_handle* h, int src, bool prestream) {
     P.pend_idx = h->pend_idx;
     P.pend_count = h->pend_count;
     P.grid_blocks = h->grid_blocks;
+    P.tile_counter = h->tile_counter;
     return P;
 }
 
@@ -190,7 +197,7 @@ int queue_step(lb_handle* h, int src, bool prestream, bool timed) {
         if (!e0 || !e1) return fail(LB_ERR_CUDA, "cudaEventCreate failed");
         CK(cudaEventRecord(e0, h->stream));
     }
-    CK(h->L.collide(P, h->tile_shape, h->stream));
+    CK(h->L.collide(P, h->tile_shape, &h->tmap[src], h->stream));
     if (timed) {
         CK(cudaEventRecord(e1, h->stream));
         h->ev_pairs[0].push_back({(int)h->ev_next - 2, (int)h->ev_next - 1});
@@ -218,6 +225,40 @@ int build_graph(lb_handle* h, int start) {
 
 bool valid_kind(int k) { return k >= LB_BB && k <= LB_PERIODIC; }
 
+// Tensor maps describing each population buffer as a 3-D array
+// (x: nx, y: ny, plane: Q) for the staged tile shapes: box = (128 + 2 H)
+// x (R + 2) x 1 elements, H = 16 bytes of halo on each side and one row
+// above and below; coordinates outside the array read as zero.
+int make_tensor_maps(lb_handle* h) {
+    const int rows = staged_rows(h->tile_shape);
+    if (h->lattice != LB_D2Q9 || rows == 0) return LB_OK;
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                         cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+            return fail(LB_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const size_t es = storage_bytes(h->prec);
+    const CUtensorMapDataType dt = h->prec == LB_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                   : h->prec == LB_F16_DEV ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                           : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const cuuint64_t gdim[3] = {(cuuint64_t)h->nx, (cuuint64_t)h->ny, (cuuint64_t)h->Q};
+    const cuuint64_t gstride[2] = {(cuuint64_t)h->nxp * es, (cuuint64_t)h->plane * es};
+    const cuuint32_t box[3] = {(cuuint32_t)(128 + 2 * (16 / es)), (cuuint32_t)(rows + 2), 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    for (int b = 0; b < 2; b++) {
+        CUresult r = encode(&h->tmap[b], dt, 3, h->buf[b], gdim, gstride, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(LB_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    }
+    return LB_OK;
+}
+
 // Persistent grid of the stream-collide kernel: resident blocks per SM for
 // the tile shape (occupancy calculator) times the SM count.
 int size_grid(lb_handle* h) {
@@ -243,7 +284,7 @@ void lb_destroy(lb_handle* h) {
     void* ptrs[] = {h->buf[0], h->buf[1], h->cand_key, h->cand_idx, h->cand_count, h->sel_idx,
                     h->sel_count, h->count_ring, h->probe_ring, h->d_step, h->d_err, h->replay_cnt,
                     h->replay_off, h->replay_idx, h->mlp, h->newton_stats, h->ticket,
-                    h->pend_idx, h->pend_count};
+                    h->pend_idx, h->pend_count, h->tile_counter};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_err) cudaFreeHost(h->h_err);
@@ -360,6 +401,8 @@ int lb_create(int lattice, int nx, int ny, int equilibrium, double nu, double de
     CKH(cudaMalloc(&h->pend_idx, std::max(1ll, nsites) * sizeof(unsigned)));
     CKH(cudaMalloc(&h->pend_count, sizeof(unsigned)));
     CKH(cudaMemsetAsync(h->pend_count, 0, sizeof(unsigned), h->stream));
+    CKH(cudaMalloc(&h->tile_counter, sizeof(unsigned)));
+    CKH(cudaMemsetAsync(h->tile_counter, 0, sizeof(unsigned), h->stream));
     CKH(cudaMallocHost(&h->h_err, sizeof(unsigned)));
     *h->h_err = 0;
     CKH(cudaEventCreateWithFlags(&h->err_ev, cudaEventDisableTiming));
@@ -371,7 +414,7 @@ int lb_create(int lattice, int nx, int ny, int equilibrium, double nu, double de
     CKH(cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), h->stream));
     CKH(cudaMemsetAsync(h->newton_stats, 0, 4 * sizeof(unsigned long long), h->stream));
     CKH(h->L.set_smem(kStageCap));
-    if (size_grid(h) != LB_OK) {
+    if (size_grid(h) != LB_OK || make_tensor_maps(h) != LB_OK) {
         const std::string msg = g_last_error;
         lb_destroy(h);
         return fail(LB_ERR_CUDA, "%s", msg.c_str());
@@ -718,7 +761,9 @@ int lb_set_tile_shape(lb_handle* h, int shape) {
     CK(cudaStreamSynchronize(h->stream));
     h->tile_shape = shape;
     drop_graphs(h);
-    return size_grid(h);
+    const int rc = size_grid(h);
+    if (rc != LB_OK) return rc;
+    return make_tensor_maps(h);
 }
 
 int lb_info(lb_handle* h, long long* out, double* beta_out) {

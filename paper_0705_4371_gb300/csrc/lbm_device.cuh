@@ -107,6 +107,7 @@ struct Params {
     unsigned* pend_idx;
     unsigned* pend_count;
     int grid_blocks;          // persistent grid size (resident blocks x SMs)
+    unsigned* tile_counter;   // next tile to hand out (staged shapes)
 };
 
 template <int Q, typename T> struct PopArr { T v[Q]; };

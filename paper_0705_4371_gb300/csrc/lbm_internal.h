@@ -9,7 +9,7 @@ namespace lbm {
 struct Params;
 
 struct Launchers {
-    cudaError_t (*collide)(const Params&, int tile_shape, cudaStream_t);
+    cudaError_t (*collide)(const Params&, int tile_shape, const void* tensor_map, cudaStream_t);
     cudaError_t (*select)(const Params&, int stage_cap, int mode, cudaStream_t);
     cudaError_t (*init_eq)(const Params&, const double* rho, const double* ux, const double* uy,
                            const double* e2, cudaStream_t);
@@ -25,7 +25,10 @@ Launchers launchers_f64(int lattice, int eq);
 Launchers launchers_f32(int lattice, int eq);
 Launchers launchers_f16(int lattice, int eq);
 
-constexpr int kTileShapes = 4;   // tile shapes of the D2Q9 stream-collide kernel
+constexpr int kTileShapes = 6;   // tile shapes of the D2Q9 stream-collide kernel
+
+// Rows per block tile of the shared-memory-staged shapes (0: not staged).
+inline int staged_rows(int tile_shape) { return tile_shape == 4 ? 8 : (tile_shape == 5 ? 4 : 0); }
 
 // message returned by lb_last_error on this thread
 void set_last_error(const char* msg);

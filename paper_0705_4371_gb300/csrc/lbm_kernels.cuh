@@ -15,6 +15,8 @@
 
 #include <algorithm>
 
+#include <cuda.h>
+
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
 
@@ -253,18 +255,22 @@ struct FinishShared {
 };
 
 // Warp-level append of pending sites to the block list (overflow: global).
-__device__ __forceinline__ void warp_pend(const Params& P, FinishShared& fs, bool pend, unsigned site) {
+__device__ __forceinline__ void warp_pend(const Params& P, unsigned* list, unsigned* nlist, bool pend,
+                                          unsigned site) {
     const unsigned m = __ballot_sync(0xffffffffu, pend);
     if (m == 0) return;
     const int lane = threadIdx.x & 31;
     unsigned base = 0;
-    if (lane == 0) base = atomicAdd(&fs.npend, (unsigned)__popc(m));
+    if (lane == 0) base = atomicAdd(nlist, (unsigned)__popc(m));
     base = __shfl_sync(0xffffffffu, base, 0);
     if (pend) {
         const unsigned slot = base + __popc(m & ((1u << lane) - 1u));
-        if (slot < (unsigned)kPend) fs.pend[slot] = site;
+        if (slot < (unsigned)kPend) list[slot] = site;
         else P.pend_idx[atomicAdd(P.pend_count, 1u)] = site;
     }
+}
+__device__ __forceinline__ void warp_pend(const Params& P, FinishShared& fs, bool pend, unsigned site) {
+    warp_pend(P, fs.pend, &fs.npend, pend, site);
 }
 
 // Exact dS of n pending sites, appending the candidates; all threads call.
@@ -285,10 +291,12 @@ __device__ void resolve_list(const Params& P, int n, SiteAt site_at) {
 }
 
 template <typename L, typename S, int EQ>
-__device__ __forceinline__ void finish_block(const Params& P, FinishShared& fs) {
-    __syncthreads();
-    const int np = (int)min(fs.npend, (unsigned)kPend);
-    if (np > 0) resolve_list<L, S, EQ>(P, np, [&](int j) { return fs.pend[j]; });
+__device__ __forceinline__ void finish_parts(const Params& P, const unsigned* pend, unsigned npend,
+                                             int& is_last, SelectShared& ss,
+                                             unsigned long long* stage_key, unsigned* stage_idx,
+                                             int stage_cap) {
+    const int np = (int)min(npend, (unsigned)kPend);
+    if (np > 0) resolve_list<L, S, EQ>(P, np, [&](int j) { return pend[j]; });
     // the barrier makes the block's writes visible to thread 0, whose
     // device-scope fence then orders all of them before the ticket
     __syncthreads();
@@ -297,10 +305,10 @@ __device__ __forceinline__ void finish_block(const Params& P, FinishShared& fs) 
         const unsigned nb = gridDim.x * gridDim.y;
         const unsigned tk = atomicAdd(P.ticket, 1u);
         __threadfence();
-        fs.is_last = (tk == nb - 1);
+        is_last = (tk == nb - 1);
     }
     __syncthreads();
-    if (fs.is_last) {
+    if (is_last) {
         const int ng = (int)__ldcg(P.pend_count);
         if (ng > 0) {
             resolve_list<L, S, EQ>(P, ng, [&](int j) { return __ldcg(P.pend_idx + j); });
@@ -308,9 +316,18 @@ __device__ __forceinline__ void finish_block(const Params& P, FinishShared& fs) 
             if (threadIdx.x == 0) *P.pend_count = 0;
         }
         __threadfence_block();
-        select_and_fix<L, S, EQ>(P, fs.ss, fs.key, fs.idx, kStage, 0);
-        if (threadIdx.x == 0) *P.ticket = 0;
+        select_and_fix<L, S, EQ>(P, ss, stage_key, stage_idx, stage_cap, 0);
+        if (threadIdx.x == 0) {
+            *P.ticket = 0;
+            if (P.tile_counter) *P.tile_counter = 0;
+        }
     }
+}
+
+template <typename L, typename S, int EQ>
+__device__ __forceinline__ void finish_block(const Params& P, FinishShared& fs) {
+    __syncthreads();
+    finish_parts<L, S, EQ>(P, fs.pend, fs.npend, fs.is_last, fs.ss, fs.key, fs.idx, kStage);
 }
 
 // Boundary site (or any site of the first step after a state upload): gather
@@ -531,6 +548,285 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_collide_d2q9(const __grid_
 }
 
 // ---------------------------------------------------------------------------
+// K1 for D2Q9 with tiles staged in shared memory by the tensor memory
+// accelerator.  A block tile is R rows x 128 sites; for each of the 9
+// population planes one 3-D bulk tensor copy brings rows y0 - 1 .. y0 + R
+// and columns x0 - H .. x0 + 128 + H (H elements = 16 bytes on each side,
+// which keeps every copy 16-byte aligned), i.e. every source any boundary
+// rule of the tile can need (except a periodic wrap).  Copies complete on an
+// mbarrier; STAGES tiles are in flight per block, so the bytes in flight do
+// not depend on registers.  Warp w computes row w of the tile, lane l the
+// sites x0 + l + 32 s (s = 0..3): shared-memory reads and global stores are
+// both consecutive across the warp.  In tiles that touch a boundary or the
+// obstacle the sites use the rule-by-rule gather from shared memory.  Every
+// wait on an mbarrier is bounded: on expiry the block flags ERR_TIMEOUT,
+// stops issuing copies, waits (bounded) for the copies it issued, and ends.
+// ---------------------------------------------------------------------------
+constexpr int kTmaTX = 128;
+constexpr long long kWaitLimit = 1ll << 22;   // try_wait polls before a wait is declared failed
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait; false when the limit expired
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+    for (long long it = 0; it < kWaitLimit; it++)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, int c0, int c1, int c2,
+                                            unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+
+template <typename S, int R>
+struct TmaLayout {
+    static constexpr int H = 16 / (int)sizeof(S);          // halo columns (16 bytes)
+    static constexpr int W = kTmaTX + 2 * H;               // staged row length
+    static constexpr int ROWS = R + 2;                     // staged rows: y0 - 1 .. y0 + R
+    static constexpr int BOX_BYTES = ROWS * W * (int)sizeof(S);
+    static constexpr int PLANE_BYTES = (BOX_BYTES + 127) / 128 * 128;   // 128-byte aligned boxes
+    static constexpr int PLANE = PLANE_BYTES / (int)sizeof(S);
+    static constexpr int STAGE_BYTES = 9 * PLANE_BYTES;
+    static constexpr int TX_BYTES = 9 * BOX_BYTES;         // bytes one tile's copies deliver
+};
+
+struct TmaShared {
+    SelectShared ss;
+    unsigned pend[kPend];
+    unsigned npend;
+    int is_last;
+    int abort;
+    int tile[8];   // tile held by each stage (-1: none left)
+};
+
+template <typename S, int R, int STAGES>
+constexpr size_t tma_smem_bytes() {
+    return 128 + (size_t)STAGES * TmaLayout<S, R>::STAGE_BYTES + 8 * STAGES + sizeof(TmaShared) + 16;
+}
+
+// Pre-collision deviations of site (x, y) of a staged tile, from shared
+// memory: the same rules as gather_site (free flight, Sec. 4.2 boundaries),
+// reading box[i][row][col] with row = y - y0 + 1, col = x - x0 + H.  Not used
+// with periodic sides (their sources lie outside the box).
+template <typename S, int R>
+__device__ __forceinline__ void gather_site_smem(const Params& P, const S* box, int x0, int y0, int x,
+                                                 int y, typename Store<S>::T* g) {
+    using L = D2Q9;
+    using T = typename Store<S>::T;
+    using LY = TmaLayout<S, R>;
+    auto at = [&](int i, int sx, int sy) {
+        return Store<S>::load(box + i * LY::PLANE + (sy - y0 + 1) * LY::W + (sx - x0 + LY::H), 0);
+    };
+    const T rho0 = Par<T>::rho0(P);
+    if (P.prestream) {
+#pragma unroll
+        for (int i = 0; i < L::Q; i++) g[i] = at(i, x, y);
+        return;
+    }
+    bool have_in = false, have_out = false;
+    T gin[L::Q], gout[L::Q];
+#pragma unroll
+    for (int i = 0; i < L::Q; i++) {
+        const int cx = L::cx(i), cy = L::cy(i);
+        const int sx = x - cx, sy = y - cy;
+        if (sx < 0 || sx >= P.nx) {
+            const int kind = sx < 0 ? P.bc[0] : P.bc[1];
+            if (kind == BC_INLET) {
+                if (!have_in) {
+                    feq_rho_u<L, T>(P.eq, (T)P.rho_in, (T)P.ux_in, (T)P.uy_in, rho0, gin);
+                    have_in = true;
+                }
+                g[i] = gin[i];
+            } else if (kind == BC_OUTLET) {
+                if (!have_out) {
+                    T drho = T(0), jx = T(0), jy = T(0);
+#pragma unroll
+                    for (int j = 0; j < L::Q; j++) {
+                        const T v = at(j, P.nx - 2, y);
+                        drho += v; jx += T(L::cx(j)) * v; jy += T(L::cy(j)) * v;
+                    }
+                    const T rho = rho0 + drho;
+                    feq_rho_u<L, T>(P.eq, rho, jx / rho, jy / rho, rho0, gout);
+                    have_out = true;
+                }
+                g[i] = gout[i];
+            } else {
+                g[i] = at(L::opp(i), x, y);
+            }
+            continue;
+        }
+        if (sy < 0 || sy >= P.ny) {
+            const int kind = sy < 0 ? P.bc[2] : P.bc[3];
+            g[i] = kind == BC_FREESLIP ? at(L::mir_y(i), sx, y) : at(L::opp(i), x, y);
+            continue;
+        }
+        g[i] = is_solid(P, sx, sy) ? at(L::opp(i), x, y) : at(i, sx, sy);
+    }
+}
+
+template <typename S, int EQ, int R, int STAGES>
+__global__ void __launch_bounds__(32 * R, 256 / R)
+    k_collide_d2q9_tma(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap tm) {
+    using L = D2Q9;
+    using T = typename Store<S>::T;
+    using LY = TmaLayout<S, R>;
+    constexpr int TX = kTmaTX;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
+    S* stages = reinterpret_cast<S*>(smem);
+    unsigned long long* full = reinterpret_cast<unsigned long long*>(smem + STAGES * LY::STAGE_BYTES);
+    TmaShared& sh = *reinterpret_cast<TmaShared*>(smem + STAGES * LY::STAGE_BYTES + 8 * STAGES);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < STAGES; st++) mbar_init(&full[st], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        sh.npend = 0;
+        sh.abort = 0;
+    }
+    __syncthreads();
+    const long long t = *P.step;
+    S* __restrict__ dst = static_cast<S*>(P.dst);
+    const int nxp = P.nxp, plane = (int)P.plane;
+    const bool periodic = P.bc[0] == BC_PERIODIC || P.bc[2] == BC_PERIODIC;
+    const int tiles_x = (P.nx + TX - 1) / TX;
+    const int tiles = tiles_x * ((P.ny + R - 1) / R);
+
+    // Tiles are handed out in row-major order by a global counter: thread 0
+    // claims one whenever it refills a stage and publishes its index with the
+    // stage's mbarrier (-1: none left; the phase is then completed by a plain
+    // arrive, without a copy).
+    auto fill = [&](int st) {
+        unsigned long long* bar = &full[st];
+        const int tile = (int)atomicAdd(P.tile_counter, 1u);
+        if (tile >= tiles) {
+            sh.tile[st] = -1;
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+            return;
+        }
+        sh.tile[st] = tile;
+        const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
+        mbar_expect_tx(bar, (unsigned)LY::TX_BYTES);
+        S* base = stages + (size_t)st * (LY::STAGE_BYTES / sizeof(S));
+#pragma unroll
+        for (int i = 0; i < L::Q; i++)
+            tma_load_3d(base + i * LY::PLANE, &tm, tx * TX - LY::H, ty * R - 1, i, bar);
+    };
+    if (threadIdx.x == 0) {
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<unsigned long long>(&tm))
+                     : "memory");
+        for (int st = 0; st < STAGES - 1; st++) fill(st);
+    }
+    bool nonfinite = false;
+    int jj = 0;
+    for (;; jj++) {
+        const int st = jj % STAGES;
+        const unsigned parity = (unsigned)((jj / STAGES) & 1);
+        // every thread waits; a wait that gave up anywhere ends the block's
+        // loop everywhere (the vote keeps the barriers matched)
+        if (__syncthreads_or(!mbar_wait(&full[st], parity))) {
+            if (threadIdx.x == 0) {
+                atomicOr(P.err, ERR_TIMEOUT);
+                sh.abort = 1;
+            }
+            break;
+        }
+        const int tile = sh.tile[st];
+        if (tile < 0) break;
+        if (threadIdx.x == 0) {
+            // the stage being refilled was last read in iteration jj - 1,
+            // whose reads the barrier at its end ordered before this point
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            fill((jj + STAGES - 1) % STAGES);
+        }
+        const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
+        const int x0 = tx * TX, y0 = ty * R;
+        const int y = y0 + warp;
+        const bool clean = !P.prestream && x0 >= 1 && x0 + TX <= P.nx - 1 && y0 >= 1 &&
+                           y0 + R <= P.ny - 1 &&
+                           (P.ow == 0 || x0 + TX + 1 <= P.ox0 || x0 - 1 >= P.ox0 + P.ow ||
+                            y0 + R + 1 <= P.oy0 || y0 - 1 >= P.oy0 + P.oh);
+        const S* box = stages + (size_t)st * (LY::STAGE_BYTES / sizeof(S));
+        const S* sb = box + (warp + 1) * LY::W + LY::H;
+#pragma unroll 1
+        for (int s = 0; s < TX / 32; s++) {
+            const int x = x0 + lane + 32 * s;
+            bool pend = false;
+            if (x < P.nx && y < P.ny) {
+                const int c = x - x0;
+                const int o = y * nxp + x;
+                bool shift = clean;
+                if (!shift) {
+                    const bool near_obstacle = P.ow > 0 && x >= P.ox0 - 1 && x <= P.ox0 + P.ow &&
+                                               y >= P.oy0 - 1 && y <= P.oy0 + P.oh;
+                    shift = !P.prestream && x >= 1 && x <= P.nx - 2 && y >= 1 && y <= P.ny - 2 &&
+                            !near_obstacle;
+                }
+                T g[L::Q];
+                bool fluid = true;
+                if (shift) {
+#pragma unroll
+                    for (int i = 0; i < L::Q; i++)
+                        g[i] = Store<S>::load(sb + i * LY::PLANE + c - L::cx(i) - L::cy(i) * LY::W, 0);
+                } else if (is_solid(P, x, y)) {
+                    fluid = false;
+#pragma unroll
+                    for (int i = 0; i < L::Q; i++) g[i] = T(0);
+                } else if (periodic) {
+                    gather_site<L, S>(P, x, y, g);
+                } else {
+                    gather_site_smem<S, R>(P, box, x0, y0, x, y, g);
+                }
+                if (fluid) pend = update_site<L, T, EQ>(P, g, x, y, t, nonfinite);
+#pragma unroll
+                for (int i = 0; i < L::Q; i++) Store<S>::store(dst + i * plane + o, 0, g[i]);
+            }
+            warp_pend(P, sh.pend, &sh.npend, pend, (unsigned)(y * P.nx + x));
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    if (sh.abort && threadIdx.x == 0) {
+        // wait (bounded) for copies still in flight into every stage
+        for (int k2 = 0; k2 < STAGES; k2++) {
+            const int j2 = jj + k2;
+            mbar_wait(&full[j2 % STAGES], (unsigned)((j2 / STAGES) & 1));
+        }
+    }
+    if (nonfinite) atomicOr(P.err, ERR_NONFINITE);
+    __syncthreads();
+    // the staged tiles are no longer needed: their memory holds the last
+    // block's candidate staging
+    const int scap = (int)min((size_t)kStage, (size_t)STAGES * LY::STAGE_BYTES / 12);
+    unsigned long long* skey = reinterpret_cast<unsigned long long*>(smem);
+    unsigned* sidx = reinterpret_cast<unsigned*>(smem + 8 * scap);
+    finish_parts<L, S, EQ>(P, sh.pend, sh.npend, sh.is_last, sh.ss, skey, sidx, scap);
+}
+
+// ---------------------------------------------------------------------------
 // K1, one site per thread (D1Q3).
 // ---------------------------------------------------------------------------
 template <typename L, typename S, int EQ>
@@ -691,17 +987,42 @@ cudaError_t occupancy_d2q9(int* per_sm) {
                                                          32 * WARPS, 0);
 }
 
+template <typename S, int EQ, int R, int STAGES>
+cudaError_t launch_d2q9_tma(const Params& P, const void* tmap, cudaStream_t st) {
+    constexpr size_t smem = tma_smem_bytes<S, R, STAGES>();
+    const long long tiles = (long long)((P.nx + kTmaTX - 1) / kTmaTX) * ((P.ny + R - 1) / R);
+    const long long want = (tiles + 3) / 4;   // at least 4 tiles per block
+    const unsigned blocks = (unsigned)std::max(1ll, std::min(want, (long long)P.grid_blocks));
+    k_collide_d2q9_tma<S, EQ, R, STAGES><<<blocks, 32 * R, smem, st>>>(
+        P, *static_cast<const CUtensorMap*>(tmap));
+    return cudaGetLastError();
+}
+
+template <typename S, int EQ, int R, int STAGES>
+cudaError_t setup_d2q9_tma(int* per_sm) {
+    constexpr size_t smem = tma_smem_bytes<S, R, STAGES>();
+    cudaError_t e = cudaFuncSetAttribute(k_collide_d2q9_tma<S, EQ, R, STAGES>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_collide_d2q9_tma<S, EQ, R, STAGES>,
+                                                         32 * R, smem);
+}
+
 template <typename L, typename S, int EQ>
 struct LaunchImpl {
-    static cudaError_t collide(const Params& P, int shape, cudaStream_t st) {
+    static cudaError_t collide(const Params& P, int shape, const void* tmap, cudaStream_t st) {
         if constexpr (L::Q == 9) {
             switch (shape) {
                 case 1: return launch_d2q9<S, EQ, 1, 8, 4>(P, st);
                 case 2: return launch_d2q9<S, EQ, 2, 8, 2>(P, st);
                 case 3: return launch_d2q9<S, EQ, 4, 8, 1>(P, st);
+                case 4: return launch_d2q9_tma<S, EQ, 8, 2>(P, tmap, st);
+                case 5: return launch_d2q9_tma<S, EQ, 4, 3>(P, tmap, st);
                 default: return launch_d2q9<S, EQ, 1, 8, 3>(P, st);
             }
         } else {
+            (void)shape;
+            (void)tmap;
             const long long N = (long long)P.nx * P.ny;
             const unsigned blocks = (unsigned)((N + kSiteBlock - 1) / kSiteBlock);
             k_collide_site<L, S, EQ><<<blocks, kSiteBlock, 0, st>>>(P);
@@ -715,6 +1036,8 @@ struct LaunchImpl {
                 case 1: return occupancy_d2q9<S, EQ, 1, 8, 4>(per_sm);
                 case 2: return occupancy_d2q9<S, EQ, 2, 8, 2>(per_sm);
                 case 3: return occupancy_d2q9<S, EQ, 4, 8, 1>(per_sm);
+                case 4: return setup_d2q9_tma<S, EQ, 8, 2>(per_sm);
+                case 5: return setup_d2q9_tma<S, EQ, 4, 3>(per_sm);
                 default: return occupancy_d2q9<S, EQ, 1, 8, 3>(per_sm);
             }
         }

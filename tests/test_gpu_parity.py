@@ -237,15 +237,19 @@ def test_beta_half_all_sites_equals_lbgk(lbm):
     assert b.counts(1)[0] == w.n_sites - w.L * w.L
 
 
-@pytest.mark.parametrize("shape", [0, 1, 2, 3])
-def test_tile_shapes_give_identical_results(lbm, shape):
-    w = small_cylinder(re=20000.0, delta=1e-6, k=16)
+@pytest.mark.parametrize("prec", ["f32", "f16dev", "f64"])
+@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4, 5])
+def test_tile_shapes_give_identical_results(lbm, shape, prec):
+    # 328 x 150: several 128-site tiles per row, ragged in x and y, obstacle
+    # and all boundary kinds inside staged tiles
+    w = small_cylinder(re=20000.0, delta=1e-6, k=16, nx=328, ny=150, L=12)
     rho, ux, uy = initial_fields(w, noise=1e-3)
-    ref = gpu_run(lbm, w, "f32")
+    ref = gpu_run(lbm, w, prec)
+    ref.set_tile_shape(1)
     ref.init_equilibrium(rho, ux, uy)
     ref.step(50)
-    g = gpu_run(lbm, w, "f32")
-    lbm._check(g.L.lb_set_tile_shape(g.h, shape))
+    g = gpu_run(lbm, w, prec)
+    g.set_tile_shape(shape)
     g.init_equilibrium(rho, ux, uy)
     g.step(50)
     assert np.array_equal(ref.get_state(), g.get_state())
