@@ -301,8 +301,10 @@ int lb_create(int lattice, int nx, int ny, int equilibrium, double nu, double de
     if (lattice != LB_D1Q3 && lattice != LB_D2Q9) return fail(LB_ERR_ARG, "unknown lattice %d", lattice);
     if (equilibrium < LB_EQ_POLY || equilibrium > LB_EQ_ENTROPIC_ENERGY_MLP)
         return fail(LB_ERR_ARG, "unknown equilibrium %d", equilibrium);
-    if (equilibrium >= LB_EQ_ENTROPIC_ENERGY)
-        return fail(LB_ERR_ARG, "energy-constrained equilibria are not available in this build");
+    if (equilibrium >= LB_EQ_ENTROPIC_ENERGY && lattice != LB_D2Q9)
+        return fail(LB_ERR_ARG, "the energy-constrained equilibria are built for D2Q9");
+    if (equilibrium == LB_EQ_ENTROPIC_ENERGY_MLP)
+        return fail(LB_ERR_ARG, "the learned equilibrium is not available in this build");
     if (precision < LB_F64 || precision > LB_F16_DEV) return fail(LB_ERR_ARG, "unknown precision %d", precision);
     if (!(nu > 0.0) || !(nu < 1e30)) return fail(LB_ERR_ARG, "nu must be positive and finite");
     if (delta != delta) return fail(LB_ERR_ARG, "delta is NaN");

@@ -24,6 +24,10 @@ struct Launchers {
 Launchers launchers_f64(int lattice, int eq);
 Launchers launchers_f32(int lattice, int eq);
 Launchers launchers_f16(int lattice, int eq);
+// energy-constrained equilibria (D2Q9), one translation unit per storage
+Launchers launchers_f64_energy(int eq);
+Launchers launchers_f32_energy(int eq);
+Launchers launchers_f16_energy(int eq);
 
 constexpr int kTileShapes = 6;   // tile shapes of the D2Q9 stream-collide kernel
 

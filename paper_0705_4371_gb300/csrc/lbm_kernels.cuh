@@ -18,6 +18,7 @@
 #include <cuda.h>
 
 #include "lbm_device.cuh"
+#include "lbm_energy.cuh"
 #include "lbm_internal.h"
 
 namespace lbm {
@@ -30,6 +31,23 @@ template <typename L, typename T, int EQ>
 __device__ __forceinline__ void equilibrium(const Params& P, T drho, T rho, T ux, T uy, T* gs) {
     if constexpr (EQ == EQ_POLY) feq_poly<L, T>(drho, rho, ux, uy, gs);
     else feq_entropic<L, T>(rho, ux, uy, Par<T>::rho0(P), gs);
+}
+
+// Energy-constrained entropic f* (D2Q9 only) as deviations from the
+// moments (drho, j, 2E); Newton from the polynomial start point
+// a0 = (3 u_x, 3 u_y, 0) (the multipliers of the first-order expansion
+// about rest).
+template <typename T, int EQ>
+__device__ __forceinline__ void equilibrium_energy(const Params& P, T rho, T jx, T jy, T e2, T* gs,
+                                                   NewtonCount& nc) {
+    const double r = (double)rho, ux = (double)jx / r, uy = (double)jy / r;
+    float a[3] = {3.0f * (float)ux, 3.0f * (float)uy, 0.0f};
+    double fs[9];
+    const double stop = sizeof(T) == 8 ? 4e-15 : kNewtonTol;
+    energy_solve(r, ux, uy, (double)e2, a, fs, nc, stop);
+    const double rho0 = P.rho0;
+#pragma unroll
+    for (int i = 0; i < 9; i++) gs[i] = (T)(fs[i] - D2Q9::w(i) * rho0);
 }
 
 template <typename L, typename T>
@@ -64,11 +82,42 @@ __device__ __forceinline__ void velocity(T jx, T jy, T rho, T& ux, T& uy) {
 // Ehrenfests' step and the exports so that all round identically).
 template <typename L, typename T, int EQ>
 __device__ __forceinline__ void site_equilibrium(const Params& P, const T* g, T* gs, T& rho, T& ux,
-                                                 T& uy) {
+                                                 T& uy, NewtonCount& nc) {
     T drho, jx, jy;
     moments<L, T>(g, Par<T>::rho0(P), drho, rho, jx, jy);
     velocity<T>(jx, jy, rho, ux, uy);
-    equilibrium<L, T, EQ>(P, drho, rho, ux, uy, gs);
+    if constexpr (EQ >= EQ_ENERGY) {
+        // 2E = sum |v|^2 f = sum |v|^2 g + rho0 sum W |v|^2
+        T e2 = T(L::sum_w_c2) * Par<T>::rho0(P);
+#pragma unroll
+        for (int i = 0; i < L::Q; i++)
+            if (L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i) == 1) e2 += g[i];
+            else if (L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i) == 2) e2 += T(2) * g[i];
+        equilibrium_energy<T, EQ>(P, rho, jx, jy, e2, gs, nc);
+    } else {
+        (void)nc;
+        equilibrium<L, T, EQ>(P, drho, rho, ux, uy, gs);
+    }
+}
+template <typename L, typename T, int EQ>
+__device__ __forceinline__ void site_equilibrium(const Params& P, const T* g, T* gs, T& rho, T& ux,
+                                                 T& uy) {
+    NewtonCount nc = {0, 0, 0, 0};
+    site_equilibrium<L, T, EQ>(P, g, gs, rho, ux, uy, nc);
+}
+
+// Per-thread Newton counts flushed to the run's statistics (energy forms).
+__device__ __forceinline__ void flush_newton(const Params& P, NewtonCount& nc) {
+    unsigned v[4] = {nc.it32, nc.it64, nc.sites, nc.fails};
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[j] += __shfl_xor_sync(0xffffffffu, v[j], o);
+    }
+    if ((threadIdx.x & 31) == 0 && v[2] > 0) {
+        for (int j = 0; j < 4; j++) atomicAdd(P.newton_stats + j, (unsigned long long)v[j]);
+        if (v[3] > 0) atomicOr(P.err, ERR_NEWTON);
+    }
 }
 
 // FP64 recomputation of dS from the stored populations (precision form).
@@ -79,8 +128,21 @@ __device__ __noinline__ double delta_s_fp64(PopArr<L::Q, T> g, double rho0) {
     for (int i = 0; i < L::Q; i++) gd[i] = (double)g.v[i];
     moments<L, double>(gd, rho0, drho, rho, jx, jy);
     velocity<double>(jx, jy, rho, ux, uy);
-    if constexpr (EQ == EQ_POLY) feq_poly<L, double>(drho, rho, ux, uy, gs);
-    else feq_entropic<L, double>(rho, ux, uy, rho0, gs);
+    if constexpr (EQ >= EQ_ENERGY) {
+        double e2 = L::sum_w_c2 * rho0;
+#pragma unroll
+        for (int i = 0; i < L::Q; i++) e2 += (double)(L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i)) * gd[i];
+        float a[3] = {3.0f * (float)ux, 3.0f * (float)uy, 0.0f};
+        double fs[9];
+        NewtonCount nc = {0, 0, 0, 0};
+        energy_solve(rho, ux, uy, e2, a, fs, nc, 4e-15);
+#pragma unroll
+        for (int i = 0; i < L::Q; i++) gs[i] = fs[i] - L::w(i) * rho0;
+    } else if constexpr (EQ == EQ_POLY) {
+        feq_poly<L, double>(drho, rho, ux, uy, gs);
+    } else {
+        feq_entropic<L, double>(rho, ux, uy, rho0, gs);
+    }
     return delta_s_exact<L, double>(gd, gs, rho0);
 }
 
@@ -90,9 +152,9 @@ __device__ __noinline__ double delta_s_fp64(PopArr<L::Q, T> g, double rho0) {
 // its exact dS is then evaluated later from the unchanged source field.
 template <typename L, typename T, int EQ>
 __device__ __forceinline__ bool update_site(const Params& P, T* g, int x, int y, long long t,
-                                            bool& nonfinite) {
+                                            bool& nonfinite, NewtonCount& nc) {
     T gs[L::Q], rho, ux, uy;
-    site_equilibrium<L, T, EQ>(P, g, gs, rho, ux, uy);
+    site_equilibrium<L, T, EQ>(P, g, gs, rho, ux, uy, nc);
     nonfinite |= !isfinite(rho + ux + uy);
     if (x == P.probe_x && y == P.probe_y && P.probe_ring)
         P.probe_ring[t % P.ring_cap] = (double)ux;
@@ -340,12 +402,24 @@ __device__ __noinline__ int boundary_site(const Params& P, int x, int y, long lo
     const long long o = (long long)y * P.nxp + x;
     T g[L::Q];
     bool nonfinite = false, pending = false;
+    NewtonCount nc = {0, 0, 0, 0};
     if (is_solid(P, x, y)) {
 #pragma unroll
         for (int i = 0; i < L::Q; i++) g[i] = T(0);
     } else {
         gather_site<L, S>(P, x, y, g);
-        pending = update_site<L, T, EQ>(P, g, x, y, t, nonfinite);
+        pending = update_site<L, T, EQ>(P, g, x, y, t, nonfinite, nc);
+    }
+    if constexpr (EQ >= EQ_ENERGY) {
+        if (nc.sites) {
+            atomicAdd(P.newton_stats + 0, (unsigned long long)nc.it32);
+            atomicAdd(P.newton_stats + 1, (unsigned long long)nc.it64);
+            atomicAdd(P.newton_stats + 2, (unsigned long long)nc.sites);
+            if (nc.fails) {
+                atomicAdd(P.newton_stats + 3, (unsigned long long)nc.fails);
+                atomicOr(P.err, ERR_NEWTON);
+            }
+        }
     }
 #pragma unroll
     for (int i = 0; i < L::Q; i++) Store<S>::store(P.dst, i * P.plane + o, g[i]);
@@ -488,6 +562,7 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_collide_d2q9(const __grid_
     int w = t0 + warp;
     int y = w / tiles_x, xt = w - y * tiles_x;
     bool nonfinite = false;
+    NewtonCount nc = {0, 0, 0, 0};
     for (; w < t1; w += WARPS) {
         const int x0 = xt * TX;
         const int xs = x0 + lane * VEC;
@@ -520,7 +595,7 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_collide_d2q9(const __grid_
             }
             bool pend[VEC];
 #pragma unroll
-            for (int s = 0; s < VEC; s++) pend[s] = update_site<L, T, EQ>(P, g[s], xs + s, y, t, nonfinite);
+            for (int s = 0; s < VEC; s++) pend[s] = update_site<L, T, EQ>(P, g[s], xs + s, y, t, nonfinite, nc);
 #pragma unroll
             for (int i = 0; i < L::Q; i++) {
                 T v[VEC];
@@ -544,6 +619,7 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_collide_d2q9(const __grid_
         while (xt >= tiles_x) { xt -= tiles_x; y++; }
     }
     if (nonfinite) atomicOr(P.err, ERR_NONFINITE);
+    if constexpr (EQ >= EQ_ENERGY) flush_newton(P, nc);
     finish_block<L, S, EQ>(P, fs);
 }
 
@@ -689,7 +765,7 @@ __device__ __forceinline__ void gather_site_smem(const Params& P, const S* box, 
 }
 
 template <typename S, int EQ, int R, int STAGES>
-__global__ void __launch_bounds__(32 * R, 256 / R)
+__global__ void __launch_bounds__(32 * R, 16 / R)
     k_collide_d2q9_tma(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap tm) {
     using L = D2Q9;
     using T = typename Store<S>::T;
@@ -741,6 +817,7 @@ __global__ void __launch_bounds__(32 * R, 256 / R)
         for (int st = 0; st < STAGES - 1; st++) fill(st);
     }
     bool nonfinite = false;
+    NewtonCount nc = {0, 0, 0, 0};
     int jj = 0;
     for (;; jj++) {
         const int st = jj % STAGES;
@@ -800,7 +877,7 @@ __global__ void __launch_bounds__(32 * R, 256 / R)
                 } else {
                     gather_site_smem<S, R>(P, box, x0, y0, x, y, g);
                 }
-                if (fluid) pend = update_site<L, T, EQ>(P, g, x, y, t, nonfinite);
+                if (fluid) pend = update_site<L, T, EQ>(P, g, x, y, t, nonfinite, nc);
 #pragma unroll
                 for (int i = 0; i < L::Q; i++) Store<S>::store(dst + i * plane + o, 0, g[i]);
             }
@@ -817,6 +894,7 @@ __global__ void __launch_bounds__(32 * R, 256 / R)
         }
     }
     if (nonfinite) atomicOr(P.err, ERR_NONFINITE);
+    if constexpr (EQ >= EQ_ENERGY) flush_newton(P, nc);
     __syncthreads();
     // the staged tiles are no longer needed: their memory holds the last
     // block's candidate staging
@@ -841,10 +919,11 @@ __global__ void __launch_bounds__(kSiteBlock) k_collide_site(const __grid_consta
     const bool inside = sid < (long long)P.nx * P.ny;
     const bool valid = inside && !is_solid(P, x, y);
     bool nonfinite = false, pending = false;
+    NewtonCount nc = {0, 0, 0, 0};
     T g[L::Q];
     if (valid) {
         gather_site<L, S>(P, x, y, g);
-        pending = update_site<L, T, EQ>(P, g, x, y, t, nonfinite);
+        pending = update_site<L, T, EQ>(P, g, x, y, t, nonfinite, nc);
     }
     if (inside) {
         const long long o = (long long)y * P.nxp + x;
@@ -883,7 +962,7 @@ __global__ void __launch_bounds__(256) k_emit_from_ds(const __grid_constant__ Pa
 // Quasiequilibrium of given (rho, u) at every fluid site; zero elsewhere.
 template <typename L, typename S, int EQ>
 __global__ void k_init_eq(const __grid_constant__ Params P, const double* rho, const double* ux,
-                          const double* uy) {
+                          const double* uy, const double* e2) {
     using T = typename Store<S>::T;
     const long long sid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (sid >= (long long)P.nx * P.ny) return;
@@ -895,7 +974,16 @@ __global__ void k_init_eq(const __grid_constant__ Params P, const double* rho, c
         for (int i = 0; i < L::Q; i++) gs[i] = T(0);
     } else {
         const T r = T(rho[sid]), u = T(ux[sid]), v = uy ? T(uy[sid]) : T(0);
-        equilibrium<L, T, EQ>(P, r - Par<T>::rho0(P), r, u, v, gs);
+        if constexpr (EQ >= EQ_ENERGY) {
+            if (e2) {
+                NewtonCount nc = {0, 0, 0, 0};
+                equilibrium_energy<T, EQ>(P, r, r * u, r * v, T(e2[sid]), gs, nc);
+            } else {
+                feq_entropic<L, T>(r, u, v, Par<T>::rho0(P), gs);   // isothermal energy
+            }
+        } else {
+            equilibrium<L, T, EQ>(P, r - Par<T>::rho0(P), r, u, v, gs);
+        }
     }
 #pragma unroll
     for (int i = 0; i < L::Q; i++) Store<S>::store(P.dst, i * P.plane + o, gs[i]);
@@ -1011,7 +1099,11 @@ cudaError_t setup_d2q9_tma(int* per_sm) {
 template <typename L, typename S, int EQ>
 struct LaunchImpl {
     static cudaError_t collide(const Params& P, int shape, const void* tmap, cudaStream_t st) {
-        if constexpr (L::Q == 9) {
+        if constexpr (L::Q == 9 && EQ >= EQ_ENERGY) {
+            // the energy forms are built for one register-fed and one staged shape
+            if (shape >= 4) return launch_d2q9_tma<S, EQ, 8, 2>(P, tmap, st);
+            return launch_d2q9<S, EQ, 1, 8, 4>(P, st);
+        } else if constexpr (L::Q == 9) {
             switch (shape) {
                 case 1: return launch_d2q9<S, EQ, 1, 8, 4>(P, st);
                 case 2: return launch_d2q9<S, EQ, 2, 8, 2>(P, st);
@@ -1031,7 +1123,10 @@ struct LaunchImpl {
     }
     static cudaError_t occupancy(int shape, int* per_sm) {
         *per_sm = 1;
-        if constexpr (L::Q == 9) {
+        if constexpr (L::Q == 9 && EQ >= EQ_ENERGY) {
+            if (shape >= 4) return setup_d2q9_tma<S, EQ, 8, 2>(per_sm);
+            return occupancy_d2q9<S, EQ, 1, 8, 4>(per_sm);
+        } else if constexpr (L::Q == 9) {
             switch (shape) {
                 case 1: return occupancy_d2q9<S, EQ, 1, 8, 4>(per_sm);
                 case 2: return occupancy_d2q9<S, EQ, 2, 8, 2>(per_sm);
@@ -1049,9 +1144,9 @@ struct LaunchImpl {
         return cudaGetLastError();
     }
     static cudaError_t init_eq(const Params& P, const double* rho, const double* ux,
-                               const double* uy, const double*, cudaStream_t st) {
+                               const double* uy, const double* e2, cudaStream_t st) {
         const long long N = (long long)P.nx * P.ny;
-        k_init_eq<L, S, EQ><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(P, rho, ux, uy);
+        k_init_eq<L, S, EQ><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(P, rho, ux, uy, e2);
         return cudaGetLastError();
     }
     static cudaError_t import_state(const Params& P, const double* f, cudaStream_t st) {
@@ -1083,14 +1178,22 @@ struct LaunchImpl {
     }
 };
 
+// Polynomial and entropic (mass and momentum) equilibria of one storage
+// type; the energy forms are instantiated in their own translation units.
 template <typename S>
-Launchers launchers_for(int lattice, int eq) {
+Launchers launchers_basic(int lattice, int eq) {
     if (lattice == 0) {
         if (eq == EQ_POLY) return LaunchImpl<D1Q3, S, EQ_POLY>::get();
         return LaunchImpl<D1Q3, S, EQ_ENTROPIC>::get();
     }
     if (eq == EQ_POLY) return LaunchImpl<D2Q9, S, EQ_POLY>::get();
     return LaunchImpl<D2Q9, S, EQ_ENTROPIC>::get();
+}
+
+template <typename S>
+Launchers launchers_energy(int eq) {
+    if (eq == EQ_ENERGY_MLP) return LaunchImpl<D2Q9, S, EQ_ENERGY_MLP>::get();
+    return LaunchImpl<D2Q9, S, EQ_ENERGY>::get();
 }
 
 }  // namespace lbm

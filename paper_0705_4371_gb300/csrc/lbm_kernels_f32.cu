@@ -2,5 +2,8 @@
 #include "lbm_kernels.cuh"
 
 namespace lbm {
-Launchers launchers_f32(int lattice, int eq) { return launchers_for<float>(lattice, eq); }
+Launchers launchers_f32(int lattice, int eq) {
+    if (lattice == 1 && eq >= EQ_ENERGY) return launchers_f32_energy(eq);
+    return launchers_basic<float>(lattice, eq);
+}
 }  // namespace lbm

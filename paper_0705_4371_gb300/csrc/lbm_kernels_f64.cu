@@ -3,7 +3,10 @@
 #include "lbm_kernels.cuh"
 
 namespace lbm {
-Launchers launchers_f64(int lattice, int eq) { return launchers_for<double>(lattice, eq); }
+Launchers launchers_f64(int lattice, int eq) {
+    if (lattice == 1 && eq >= EQ_ENERGY) return launchers_f64_energy(eq);
+    return launchers_basic<double>(lattice, eq);
+}
 }  // namespace lbm
 
 namespace lbm {
