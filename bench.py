@@ -284,6 +284,9 @@ def run_gpu(args):
                                 "collide_frac": round(ach / peaks["hbm_gbs"], 4),
                                 "bytes_per_site": inf2["bytes_per_site"]}
 
+    if args.forms and args.learned and rank == 0:
+        forms["learned"] = learned_form(args, stream)
+
     cpu = cpu_baseline(w, args) if (rank == 0 and world == 1 and not args.no_cpu) else None
     clk = clocks.summary()
     line = {
@@ -316,6 +319,57 @@ def run_gpu(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def learned_form(args, stream):
+    """Energy-constrained entropic run (2048 x 1024 cylinder, L = 64,
+    Re = 5000, delta = 1e-3, k = 64, FP32 storage; initial energy = the
+    isothermal energy x (1 + 0.1 sin(2 pi y/ny) cos(2 pi x/nx))) with the
+    Newton solve started from the polynomial point and from the trained
+    network: MLUPS and Newton iterations per site of each, and the network's
+    training cost (1e7 samples on the GPU)."""
+    import torch
+    from paper_0705_4371_gb300 import learned, lbm
+    t0 = time.perf_counter()
+    params, info = learned.train_energy_mlp(n=args.mlp_samples, epochs=args.mlp_epochs, batch=4096,
+                                            lr0=2e-3, lr1=2e-5)
+    train_s = time.perf_counter() - t0
+    w = inputs.workload_c4()
+    rho, ux, uy = inputs.cylinder_fields(w)
+    with lbm.Lattice.from_workload(w, precision=lbm.LB_F64, stream=stream.cuda_stream) as iso:
+        iso.init_equilibrium(rho, ux, uy)
+        e2 = iso.moments()[3] * inputs.energy_factor(w)
+    out = {"workload": w.name, "storage": "f32", "train": {
+        "samples": args.mlp_samples, "epochs": args.mlp_epochs, "batch": 4096,
+        "final_loss": info["losses"][-1], "seconds": round(train_s, 2),
+        "dataset_newton_fp32_it_per_sample": round(info["dataset_stats"][0] / info["dataset_stats"][2], 3)}}
+    for name, eq in (("newton", lbm.LB_EQ_ENTROPIC_ENERGY), ("mlp_warm_start", lbm.LB_EQ_ENTROPIC_ENERGY_MLP)):
+        with lbm.Lattice.from_workload(w, precision=lbm.LB_F32, equilibrium=eq,
+                                       stream=stream.cuda_stream) as h2:
+            if eq == lbm.LB_EQ_ENTROPIC_ENERGY_MLP:
+                h2.set_mlp(params)
+            h2.init_equilibrium(rho, ux, uy, e2)
+            h2.set_timing(True)
+            h2.step(args.learned_warmup)
+            h2.sync()
+            h2.kernel_times(reset=True)
+            h2.newton_stats(reset=True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h2.step(args.learned_steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            fms = e0.elapsed_time(e1)
+            k2 = h2.kernel_times(reset=True)
+            it32, it64, sites, fails = h2.newton_stats(reset=True)
+            out[name] = {"MLUPS": round(w.n_sites * args.learned_steps / (fms * 1e-3) / 1e6, 1),
+                         "ms_per_step": round(fms / args.learned_steps, 4),
+                         "collide_ms": round(k2["collide_ms"] / max(k2["collide_launches"], 1), 4),
+                         "newton_fp32_it_per_site": round(it32 / max(sites, 1), 4),
+                         "newton_fp64_it_per_site": round(it64 / max(sites, 1), 4),
+                         "newton_fails": int(fails), "steps": args.learned_steps}
+    out["speedup"] = round(out["mlp_warm_start"]["MLUPS"] / out["newton"]["MLUPS"], 4)
+    return out
 
 
 # --------------------------------------------------------------------------
@@ -405,6 +459,11 @@ def main():
     ap.add_argument("--tile-shape", type=int, default=-1)
     ap.add_argument("--forms", type=int, default=1)
     ap.add_argument("--form-steps", type=int, default=2000)
+    ap.add_argument("--learned", type=int, default=1)
+    ap.add_argument("--learned-steps", type=int, default=400)
+    ap.add_argument("--learned-warmup", type=int, default=20)
+    ap.add_argument("--mlp-samples", type=int, default=10_000_000)
+    ap.add_argument("--mlp-epochs", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=150.0)
     ap.add_argument("--no-cpu", action="store_true")

@@ -208,12 +208,77 @@ int lb_select_only_noalloc(const double* ds, int n, double delta, int k, int* id
  * for step t, their indices concatenated in idx.  Host arrays. */
 int lb_replay_selection(lb_handle* h, const int* counts, const int* idx, int nsteps);
 
-/* Network for LB_EQ_ENTROPIC_ENERGY_MLP: n = lb_mlp_param_count() FP32
- * parameters (W1[64][4], b1[64], W2[64][64], b2[64], W3[4][64], b3[4],
- * then the 8 input normalisation constants (mean[4], inv_std[4]) and the
- * 4 output scales), host array; rounded to BF16 for inference. */
+/* ---- Learned form ------------------------------------------------------
+ * The 4-64-64-4 ReLU network that gives the energy Newton solve of
+ * LB_EQ_ENTROPIC_ENERGY_MLP its start point.  The Lagrange form of the
+ * quasiequilibrium (Sec. 3.3) is ln(f*_i / W_i) = mu . (1, v_x, v_y, |v|^2);
+ * the network maps the standardised features (rho, u_x, u_y,
+ * 2E/rho - |u|^2) to (mu - mu0) / out_scale, mu0 = (ln rho - 3/2 |u|^2,
+ * 3 u_x, 3 u_y, 0) being the polynomial start point.  The paper does not
+ * use a network; it is this implementation's way to shorten the solve.
+ *
+ * Parameters: n = lb_mlp_param_count() FP32 values, in this order:
+ * W1[64][4], b1[64], W2[64][64], b2[64], W3[4][64], b3[4] (trainable), then
+ * mean[4], inv_std[4] (input standardisation) and out_scale[4].  Evaluation
+ * (inference and the forward pass of training) rounds the standardised
+ * inputs, the weights and the hidden activations to BF16 and accumulates in
+ * FP32 on the tensor cores.
+ *
+ * lb_set_mlp: host array of n parameters (all finite), copied into the
+ * run (the run must use LB_EQ_ENTROPIC_ENERGY_MLP; lb_step fails with
+ * LB_ERR_STATE until it has been called).  Synchronises the run's stream. */
 int lb_mlp_param_count(void);
 int lb_set_mlp(lb_handle* h, const float* params, int n);
+
+/* Initial parameters (host array of n = lb_mlp_param_count()): weights
+ * uniform in +-sqrt(6 / fan_in) from SplitMix64(seed), zero biases,
+ * mean 0, inv_std 1, out_scale 1. */
+int lb_mlp_init(float* params, int n, unsigned long long seed);
+
+/* Training data (Sec. 3.3 with the moments M = (rho, rho u, 2E) of
+ * (argmax)).  Device arrays of n samples: rho, ux, uy and escale; sample i
+ * has 2E = escale[i] x (2E of the isothermal entropic equilibrium of
+ * Sec. 4.2 at rho, u).  Its multipliers mu are found by Newton from mu0
+ * (FP32 iterations, FP64 steps to a residual of 1e-12 or below).  Outputs
+ * (device): feat[n][4] = (rho, u_x, u_y, 2E/rho - |u|^2) and
+ * dmu[n][4] = mu - mu0 (FP32); mu[n][4] (FP64, optional); stats (optional,
+ * 4 counters, added to): FP32 iterations, FP64 iterations, samples, samples
+ * whose residual missed 1e-12.  Asynchronous on the stream (NULL: the
+ * default stream). */
+int lb_energy_dataset(const double* rho, const double* ux, const double* uy, const double* escale,
+                      long long n, float* feat, float* dmu, double* mu, unsigned long long* stats,
+                      void* cuda_stream);
+
+/* Sets mean, inv_std (1 / standard deviation) of the features and out_scale
+ * (root mean square of dmu) of the device parameter vector from n samples
+ * (device arrays as written by lb_energy_dataset).  Asynchronous. */
+int lb_mlp_normalise(float* params, const float* feat, const float* dmu, long long n, void* cuda_stream);
+
+/* The network's outputs y[n][4] for features feat[n][4]; device arrays,
+ * asynchronous. */
+int lb_mlp_forward(const float* params, const float* feat, long long n, float* y, void* cuda_stream);
+
+/* Loss L = mean over the n samples and the 4 outputs of
+ * (y - dmu / out_scale)^2 and its gradient with respect to the parameters
+ * (grad[lb_mlp_param_count()]; the normalisation entries get 0), taken
+ * through the BF16 roundings as if they were the identity.  Device arrays;
+ * loss: one float (device, may be NULL).  Deterministic.  Asynchronous. */
+int lb_mlp_grad(const float* params, const float* feat, const float* dmu, int n, float* grad,
+                float* loss, void* cuda_stream);
+
+/* One Adam step t >= 1 (b1 = 0.9, b2 = 0.999, eps = 1e-8) on the trainable
+ * entries: m, v are the moment estimates (device, lb_mlp_param_count()
+ * floats each, zero before step 1).  Asynchronous. */
+int lb_mlp_adam(float* params, const float* grad, float* m, float* v, long long t, double lr,
+                void* cuda_stream);
+
+/* Mini-batch Adam over n samples (consecutive batches of `batch`, the last
+ * one shorter), `epochs` passes; the learning rate decays geometrically
+ * from lr0 at the first step to lr1 at the last.  params (device) in and
+ * out; loss_log (device, optional): mean batch loss of each epoch.
+ * Asynchronous; allocates its working memory on the stream. */
+int lb_mlp_train(float* params, const float* feat, const float* dmu, long long n, int batch, int epochs,
+                 double lr0, double lr1, float* loss_log, void* cuda_stream);
 
 /* Newton statistics of the energy forms since the last reset: total
  * FP32 and FP64 iterations, sites solved, and sites that missed 1e-12. */

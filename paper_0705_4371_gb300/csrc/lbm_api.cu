@@ -16,6 +16,7 @@
 #include "../../include/lbm.h"
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
+#include "lbm_mlp.cuh"
 
 using namespace lbm;
 
@@ -45,6 +46,9 @@ constexpr int kStageCap = 8192;      // candidates staged in shared memory by th
 constexpr int kGraphSteps = 32;      // steps per captured graph (even: buffers return)
 constexpr int kDefaultLog = 65536;
 constexpr int kDefaultTileShape = 4;  // fastest measured on GB300 (staged tiles, 2 in flight)
+// The energy forms are bound by the Newton solve, not by memory: more
+// resident warps (register-fed shape 1) hide its FP64 latency better.
+constexpr int kDefaultTileShapeEnergy = 1;
 
 size_t storage_bytes(int prec) { return prec == LB_F64 ? 8 : (prec == LB_F16_DEV ? 2 : 4); }
 
@@ -97,8 +101,9 @@ struct lb_handle {
     size_t ev_next;
     double acc_ms[2];
     long long acc_n[2];
-    // energy form
+    // energy form; the learned form's network (FP32 master copy on the device)
     float* mlp;
+    bool mlp_set;
     unsigned long long* newton_stats;
     // completion ticket of the stream-collide blocks; tile shape of K1
     unsigned* ticket;
@@ -303,8 +308,6 @@ int lb_create(int lattice, int nx, int ny, int equilibrium, double nu, double de
         return fail(LB_ERR_ARG, "unknown equilibrium %d", equilibrium);
     if (equilibrium >= LB_EQ_ENTROPIC_ENERGY && lattice != LB_D2Q9)
         return fail(LB_ERR_ARG, "the energy-constrained equilibria are built for D2Q9");
-    if (equilibrium == LB_EQ_ENTROPIC_ENERGY_MLP)
-        return fail(LB_ERR_ARG, "the learned equilibrium is not available in this build");
     if (precision < LB_F64 || precision > LB_F16_DEV) return fail(LB_ERR_ARG, "unknown precision %d", precision);
     if (!(nu > 0.0) || !(nu < 1e30)) return fail(LB_ERR_ARG, "nu must be positive and finite");
     if (delta != delta) return fail(LB_ERR_ARG, "delta is NaN");
@@ -353,7 +356,8 @@ int lb_create(int lattice, int nx, int ny, int equilibrium, double nu, double de
     h->bc = b;
     h->plane = (long long)ny * h->nxp;
     h->probe_x = h->probe_y = -1;
-    h->tile_shape = lattice == LB_D2Q9 ? kDefaultTileShape : 0;
+    h->tile_shape = lattice != LB_D2Q9 ? 0
+                    : equilibrium >= LB_EQ_ENTROPIC_ENERGY ? kDefaultTileShapeEnergy : kDefaultTileShape;
     h->ring_cap = kDefaultLog;
     h->replay_t0 = -1;
     if (precision == LB_F64) h->L = launchers_f64(lattice, equilibrium);
@@ -398,6 +402,10 @@ int lb_create(int lattice, int nx, int ny, int equilibrium, double nu, double de
     CKH(cudaMalloc(&h->d_step, sizeof(long long)));
     CKH(cudaMalloc(&h->d_err, sizeof(unsigned)));
     CKH(cudaMalloc(&h->newton_stats, 4 * sizeof(unsigned long long)));
+    if (h->eq == LB_EQ_ENTROPIC_ENERGY_MLP) {
+        CKH(cudaMalloc(&h->mlp, lbm::kMlpParams * sizeof(float)));
+        CKH(cudaMemsetAsync(h->mlp, 0, lbm::kMlpParams * sizeof(float), h->stream));
+    }
     CKH(cudaMalloc(&h->ticket, sizeof(unsigned)));
     CKH(cudaMemsetAsync(h->ticket, 0, sizeof(unsigned), h->stream));
     CKH(cudaMalloc(&h->pend_idx, std::max(1ll, nsites) * sizeof(unsigned)));
@@ -514,6 +522,8 @@ int lb_step(lb_handle* h, int n) {
     if (n < 0) return fail(LB_ERR_ARG, "n must be >= 0");
     int rc = check_sticky(h, false);
     if (rc != LB_OK) return rc;
+    if (h->eq == LB_EQ_ENTROPIC_ENERGY_MLP && !h->mlp_set)
+        return fail(LB_ERR_STATE, "the learned equilibrium needs its network (lb_set_mlp) first");
     int done = 0;
     const bool replaying = h->replay_n > 0 && h->h_step < h->replay_t0 + h->replay_n;
     while (done < n) {
@@ -703,12 +713,19 @@ int lb_select_only(const double* ds, int n, double delta, int k, int* idx_out, i
     return LB_OK;
 }
 
-int lb_mlp_param_count(void) { return 64 * 4 + 64 + 64 * 64 + 64 + 4 * 64 + 4 + 8 + 4; }
+int lb_mlp_param_count(void) { return lbm::kMlpParams; }
 
 int lb_set_mlp(lb_handle* h, const float* params, int n) {
     if (!h || !params) return fail(LB_ERR_ARG, "NULL argument");
     if (n != lb_mlp_param_count()) return fail(LB_ERR_ARG, "expected %d parameters", lb_mlp_param_count());
-    return fail(LB_ERR_STATE, "the learned equilibrium is not available in this build");
+    if (h->eq != LB_EQ_ENTROPIC_ENERGY_MLP)
+        return fail(LB_ERR_STATE, "the run does not use the learned equilibrium");
+    for (int i = 0; i < n; i++)
+        if (!std::isfinite(params[i])) return fail(LB_ERR_ARG, "parameter %d is not finite", i);
+    CK(cudaMemcpyAsync(h->mlp, params, (size_t)n * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->mlp_set = true;
+    return LB_OK;
 }
 
 int lb_newton_stats(lb_handle* h, long long* it32, long long* it64, long long* sites,

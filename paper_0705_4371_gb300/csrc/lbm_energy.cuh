@@ -8,11 +8,18 @@
 // Newton: a <- a - C^{-1} (E[m'] - t), C the covariance of m' under p
 // (symmetric positive definite: the dual is strictly convex, so the root is
 // unique and the start point only changes the iteration count).
-// Iterations run in FP32 until |E[m'] - t| <= 2e-6; then FP64 steps take
-// the residual to <= 1e-12 (max-norm of m(f*) - M over rho).  The FP64
-// exponentials are evaluated once, at the FP32 solution; later updates
-// multiply them by e^{-delta} from its Taylor series, exact to rounding
-// for the tiny FP64 steps.
+// The FP32 phase iterates until the residual |E[m'] - t| is at or below
+// 2e-6 and no longer falls fourfold per step (FP32's noise floor, about
+// 1e-7), or is below 3e-7.  The FP64 phase then takes Newton steps with the
+// residual evaluated in FP64 and the covariance and the 3 x 3 solve in FP32
+// (an approximate Jacobian keeps the convergence: its relative error of
+// about 1e-7 adds 1e-7 x the residual per step), until the residual (max-norm
+// of m(f*) - M over rho) is at or below 1e-12.  GB300's FP64 pipe is slow,
+// so the FP64 phase avoids FP64 exponentials, divisions and square roots:
+// it starts from the FP32 exponentials b = e^{a} (any positive b gives a
+// member of the family above), takes reciprocals from FP32 seeds refined by
+// Newton-Raphson, and updates b by the Taylor series of e^{-delta} for the
+// tiny FP64 steps.
 #pragma once
 
 #include "lbm_device.cuh"
@@ -22,12 +29,23 @@ namespace lbm {
 constexpr int kNewton32Max = 16;
 constexpr int kNewton64Max = 6;
 constexpr float kNewton32Tol = 2e-6f;
+constexpr float kNewton32Floor = 3e-7f;
 constexpr double kNewtonTol = 1e-12;
 
 struct NewtonCount {
     unsigned it32, it64, sites, fails;
 };
 
+// 1 / x in FP64 from the FP32 reciprocal refined by two Newton-Raphson
+// steps (each squares the relative error: 2^-23 -> 2^-46 -> below one FP64
+// ulp).  x must lie in the normal FP32 range.
+__device__ __forceinline__ double recip64(double x) {
+    double r = (double)__frcp_rn((float)x);
+    double e = fma(-x, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-x, r, 1.0);
+    return fma(r, e, r);
+}
 // Unnormalised weights q_i = W_i bx^{v_x} by^{v_y} bc^{|v|^2} from
 // b = e^{a} and its reciprocals.
 template <typename U>
@@ -52,7 +70,7 @@ __device__ __forceinline__ U energy_terms(const U* q, const U* tgt, U& Z, U* g, 
     const U qa = q[1] + q[2] + q[3] + q[4];          // |v|^2 = 1
     const U qd = q[5] + q[6] + q[7] + q[8];          // |v|^2 = 2
     Z = q[0] + qa + qd;
-    const U iz = U(1) / Z;
+    const U iz = recip<U>(Z);
     const U sx = (q[1] - q[3]) + (q[5] - q[6] - q[7] + q[8]);
     const U sy = (q[2] - q[4]) + (q[5] + q[6] - q[7] - q[8]);
     const U sc = qa + U(2) * qd;
@@ -75,26 +93,42 @@ __device__ __forceinline__ U energy_terms(const U* q, const U* tgt, U& Z, U* g, 
     return fmax(fmax(fabs(g[0]), fabs(g[1])), fabs(g[2]));
 }
 
+// FP64 residual g = E[m'] - t from q; returns max |g| and Z, 1/Z.
+__device__ __forceinline__ double energy_residual64(const double* q, const double* tgt, double& Z,
+                                                    double& iz, double* g) {
+    const double qa = q[1] + q[2] + q[3] + q[4];
+    const double qd = q[5] + q[6] + q[7] + q[8];
+    Z = q[0] + qa + qd;
+    iz = recip64(Z);
+    const double sx = (q[1] - q[3]) + (q[5] - q[6] - q[7] + q[8]);
+    const double sy = (q[2] - q[4]) + (q[5] + q[6] - q[7] - q[8]);
+    const double sc = qa + 2.0 * qd;
+    g[0] = sx * iz - tgt[0];
+    g[1] = sy * iz - tgt[1];
+    g[2] = sc * iz - tgt[2];
+    return fmax(fmax(fabs(g[0]), fabs(g[1])), fabs(g[2]));
+}
+
 // Solve C d = g (3 x 3, symmetric positive definite) by Cholesky
-// factorisation.  Returns false if C is not positive definite.
-template <typename U>
-__device__ __forceinline__ bool spd3_solve(const U* C, const U* g, U* d) {
-    const U l00 = sqrt(C[0]);
-    if (!(l00 > U(0))) return false;
-    const U l10 = C[1] / l00, l20 = C[2] / l00;
-    const U s11 = C[3] - l10 * l10;
-    if (!(s11 > U(0))) return false;
-    const U l11 = sqrt(s11);
-    const U l21 = (C[4] - l20 * l10) / l11;
-    const U s22 = C[5] - l20 * l20 - l21 * l21;
-    if (!(s22 > U(0))) return false;
-    const U l22 = sqrt(s22);
-    const U y0 = g[0] / l00;
-    const U y1 = (g[1] - l10 * y0) / l11;
-    const U y2 = (g[2] - l20 * y0 - l21 * y1) / l22;
-    d[2] = y2 / l22;
-    d[1] = (y1 - l21 * d[2]) / l11;
-    d[0] = (y0 - l10 * d[1] - l20 * d[2]) / l00;
+// factorisation in FP32 with reciprocal square roots (a Newton step needs
+// no more).  Returns false if C is not positive definite.
+__device__ __forceinline__ bool spd3_solve(const float* C, const float* g, float* d) {
+    if (!(C[0] > 0.0f)) return false;
+    const float i00 = rsqrtf(C[0]);
+    const float l10 = C[1] * i00, l20 = C[2] * i00;
+    const float s11 = C[3] - l10 * l10;
+    if (!(s11 > 0.0f)) return false;
+    const float i11 = rsqrtf(s11);
+    const float l21 = (C[4] - l20 * l10) * i11;
+    const float s22 = C[5] - l20 * l20 - l21 * l21;
+    if (!(s22 > 0.0f)) return false;
+    const float i22 = rsqrtf(s22);
+    const float y0 = g[0] * i00;
+    const float y1 = (g[1] - l10 * y0) * i11;
+    const float y2 = (g[2] - l20 * y0 - l21 * y1) * i22;
+    d[2] = y2 * i22;
+    d[1] = (y1 - l21 * d[2]) * i11;
+    d[0] = (y0 - l10 * d[1] - l20 * d[2]) * i00;
     return true;
 }
 
@@ -104,67 +138,81 @@ __device__ __forceinline__ double exp_small_neg(double d) {
     return fma(fma(fma(fma(d, 1.0 / 24.0, -1.0 / 6.0), d, 0.5), d, -1.0), d, 1.0);
 }
 
-// Energy-constrained quasiequilibrium f*_i (FP64) of one site.  a: start
-// point in, solution out.  FP64 steps continue until the residual is at or
+// Energy-constrained quasiequilibrium f*_i (FP64) of one site from rho,
+// u and th = 2E / rho.  a: start point (FP32 multipliers) in, the FP32
+// phase's solution out.  FP64 steps continue until the residual is at or
 // below stop_tol (1e-12, or closer to the rounding floor for FP64 storage).
 // Returns false if the residual did not reach 1e-12 (the site then keeps
-// the last iterate).
-__device__ __forceinline__ bool energy_solve(double rho, double ux, double uy, double e2,
-                                             float* a, double* fstar, NewtonCount& nc,
-                                             double stop_tol) {
-    const double th = e2 / rho;
+// the last iterate).  a64 (optional): the solution's multipliers in FP64.
+__device__ __forceinline__ bool energy_solve(double rho, double ux, double uy, double th, float* a,
+                                             double* fstar, NewtonCount& nc, double stop_tol,
+                                             double* a64 = nullptr) {
     // FP32 phase
     const float tf[3] = {(float)ux, (float)uy, (float)th};
+    float bx = 1.0f, by = 1.0f, bc = 1.0f, rprev = INFINITY;
     int it = 0;
-    for (; it < kNewton32Max; it++) {
+    for (;; it++) {
         float q[9], Z, g[3], C[6], d[3];
-        const float bx = expf(a[0]), by = expf(a[1]), bc = expf(a[2]);
-        energy_q<float>(bx, by, bc, 1.0f / bx, 1.0f / by, q);
+        bx = expf(a[0]);
+        by = expf(a[1]);
+        bc = expf(a[2]);
+        energy_q<float>(bx, by, bc, __frcp_rn(bx), __frcp_rn(by), q);
         const float r = energy_terms<float>(q, tf, Z, g, C);
-        if (r <= kNewton32Tol) break;
-        if (!spd3_solve<float>(C, g, d)) break;
+        if (r <= kNewton32Tol && (r <= kNewton32Floor || r > 0.25f * rprev)) break;
+        if (it == kNewton32Max || !spd3_solve(C, g, d)) break;
         // damp very long steps (far start points)
         const float dm = fmaxf(fmaxf(fabsf(d[0]), fabsf(d[1])), fabsf(d[2]));
         const float sc = dm > 0.5f ? 0.5f / dm : 1.0f;
         a[0] -= sc * d[0];
         a[1] -= sc * d[1];
         a[2] -= sc * d[2];
+        rprev = r;
     }
     nc.it32 += (unsigned)it;
-    // FP64 phase
+    // FP64 phase, from the exponentials of the FP32 phase's last iterate
     const double tg[3] = {ux, uy, th};
-    double ad[3] = {(double)a[0], (double)a[1], (double)a[2]};
-    double b[3] = {exp(ad[0]), exp(ad[1]), exp(ad[2])};
-    double ib[2] = {1.0 / b[0], 1.0 / b[1]};
-    double q[9], Z = 1.0;
+    double b[3] = {(double)bx, (double)by, (double)bc};
+    double ib[2] = {recip64(b[0]), recip64(b[1])};
+    double q[9], Z = 1.0, iz = 1.0;
     bool ok = false;
     int it64 = 0;
-    for (; it64 <= kNewton64Max; it64++) {
-        double g[3], C[6], d[3];
+    for (;; it64++) {
+        double g[3];
         energy_q<double>(b[0], b[1], b[2], ib[0], ib[1], q);
-        const double r = energy_terms<double>(q, tg, Z, g, C);
+        const double r = energy_residual64(q, tg, Z, iz, g);
         ok = r <= kNewtonTol;
-        if (r <= stop_tol) break;
-        if (it64 == kNewton64Max || !spd3_solve<double>(C, g, d)) break;
-        const double dm = fmax(fmax(fabs(d[0]), fabs(d[1])), fabs(d[2]));
-        for (int j = 0; j < 3; j++) ad[j] -= d[j];
-        if (dm < 0x1p-10) {
-            for (int j = 0; j < 3; j++) b[j] *= exp_small_neg(d[j]);
-            ib[0] *= exp_small_neg(-d[0]);
-            ib[1] *= exp_small_neg(-d[1]);
+        if (r <= stop_tol || it64 == kNewton64Max) break;
+        float qf[9], Cf[6], gf[3], df[3], Zf, unused[3];
+        const float zero[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int i = 0; i < 9; i++) qf[i] = (float)q[i];
+        energy_terms<float>(qf, zero, Zf, unused, Cf);
+        gf[0] = (float)g[0];
+        gf[1] = (float)g[1];
+        gf[2] = (float)g[2];
+        if (!spd3_solve(Cf, gf, df)) break;
+        const float dm = fmaxf(fmaxf(fabsf(df[0]), fabsf(df[1])), fabsf(df[2]));
+        if (dm < 0x1p-10f) {
+            for (int j = 0; j < 3; j++) b[j] *= exp_small_neg((double)df[j]);
+            ib[0] *= exp_small_neg(-(double)df[0]);
+            ib[1] *= exp_small_neg(-(double)df[1]);
         } else {
-            for (int j = 0; j < 3; j++) b[j] = exp(ad[j]);
-            ib[0] = 1.0 / b[0];
-            ib[1] = 1.0 / b[1];
+            // a long step (the FP32 phase stopped early): damped, exact exponentials
+            const double sc = dm > 0.5f ? 0.5 / (double)dm : 1.0;
+            for (int j = 0; j < 3; j++) b[j] *= exp(-sc * (double)df[j]);
+            ib[0] = recip64(b[0]);
+            ib[1] = recip64(b[1]);
         }
     }
     nc.it64 += (unsigned)it64;
     nc.sites += 1u;
     if (!ok) nc.fails += 1u;
-    a[0] = (float)ad[0];
-    a[1] = (float)ad[1];
-    a[2] = (float)ad[2];
-    const double s = rho / Z;
+    if (a64) {
+        a64[0] = log(b[0]);
+        a64[1] = log(b[1]);
+        a64[2] = log(b[2]);
+    }
+    const double s = rho * iz;
 #pragma unroll
     for (int i = 0; i < 9; i++) fstar[i] = s * q[i];
     return ok;

@@ -19,6 +19,7 @@
 
 #include "lbm_device.cuh"
 #include "lbm_energy.cuh"
+#include "lbm_mlp.cuh"
 #include "lbm_internal.h"
 
 namespace lbm {
@@ -34,17 +35,24 @@ __device__ __forceinline__ void equilibrium(const Params& P, T drho, T rho, T ux
 }
 
 // Energy-constrained entropic f* (D2Q9 only) as deviations from the
-// moments (drho, j, 2E); Newton from the polynomial start point
-// a0 = (3 u_x, 3 u_y, 0) (the multipliers of the first-order expansion
-// about rest).
+// moments (drho, j, 2E); Newton from the start point a0 (the network's
+// warm start in the learned form) or, when a0 is null, from the polynomial
+// start point (3 u_x, 3 u_y, 0) (the multipliers of the first-order
+// expansion about rest).
 template <typename T, int EQ>
 __device__ __forceinline__ void equilibrium_energy(const Params& P, T rho, T jx, T jy, T e2, T* gs,
-                                                   NewtonCount& nc) {
-    const double r = (double)rho, ux = (double)jx / r, uy = (double)jy / r;
+                                                   NewtonCount& nc, const float* a0 = nullptr) {
+    const double r = (double)rho, ir = recip64(r);
+    const double ux = (double)jx * ir, uy = (double)jy * ir;
     float a[3] = {3.0f * (float)ux, 3.0f * (float)uy, 0.0f};
+    if (a0) {
+        a[0] = a0[0];
+        a[1] = a0[1];
+        a[2] = a0[2];
+    }
     double fs[9];
     const double stop = sizeof(T) == 8 ? 4e-15 : kNewtonTol;
-    energy_solve(r, ux, uy, (double)e2, a, fs, nc, stop);
+    energy_solve(r, ux, uy, (double)e2 * ir, a, fs, nc, stop);
     const double rho0 = P.rho0;
 #pragma unroll
     for (int i = 0; i < 9; i++) gs[i] = (T)(fs[i] - D2Q9::w(i) * rho0);
@@ -78,24 +86,32 @@ __device__ __forceinline__ void velocity(T jx, T jy, T rho, T& ux, T& uy) {
     }
 }
 
+// 2E = sum |v|^2 f = sum |v|^2 g + rho0 sum W |v|^2 of a site's deviations.
+template <typename L, typename T>
+__device__ __forceinline__ T energy_moment(const T* g, T rho0) {
+    T e2 = T(L::sum_w_c2) * rho0;
+#pragma unroll
+    for (int i = 0; i < L::Q; i++)
+        if (L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i) == 1) e2 += g[i];
+        else if (L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i) == 2) e2 += T(2) * g[i];
+    return e2;
+}
+
 // Quasiequilibrium of a gathered site (shared by the collision, the
-// Ehrenfests' step and the exports so that all round identically).
+// Ehrenfests' step and the exports so that all round identically).  a0:
+// Newton start point of the energy forms (null: the polynomial start).
 template <typename L, typename T, int EQ>
 __device__ __forceinline__ void site_equilibrium(const Params& P, const T* g, T* gs, T& rho, T& ux,
-                                                 T& uy, NewtonCount& nc) {
+                                                 T& uy, NewtonCount& nc, const float* a0 = nullptr) {
     T drho, jx, jy;
     moments<L, T>(g, Par<T>::rho0(P), drho, rho, jx, jy);
     velocity<T>(jx, jy, rho, ux, uy);
     if constexpr (EQ >= EQ_ENERGY) {
-        // 2E = sum |v|^2 f = sum |v|^2 g + rho0 sum W |v|^2
-        T e2 = T(L::sum_w_c2) * Par<T>::rho0(P);
-#pragma unroll
-        for (int i = 0; i < L::Q; i++)
-            if (L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i) == 1) e2 += g[i];
-            else if (L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i) == 2) e2 += T(2) * g[i];
-        equilibrium_energy<T, EQ>(P, rho, jx, jy, e2, gs, nc);
+        const T e2 = energy_moment<L, T>(g, Par<T>::rho0(P));
+        equilibrium_energy<T, EQ>(P, rho, jx, jy, e2, gs, nc, a0);
     } else {
         (void)nc;
+        (void)a0;
         equilibrium<L, T, EQ>(P, drho, rho, ux, uy, gs);
     }
 }
@@ -135,7 +151,7 @@ __device__ __noinline__ double delta_s_fp64(PopArr<L::Q, T> g, double rho0) {
         float a[3] = {3.0f * (float)ux, 3.0f * (float)uy, 0.0f};
         double fs[9];
         NewtonCount nc = {0, 0, 0, 0};
-        energy_solve(rho, ux, uy, e2, a, fs, nc, 4e-15);
+        energy_solve(rho, ux, uy, e2 / rho, a, fs, nc, 4e-15);
 #pragma unroll
         for (int i = 0; i < L::Q; i++) gs[i] = fs[i] - L::w(i) * rho0;
     } else if constexpr (EQ == EQ_POLY) {
@@ -152,9 +168,10 @@ __device__ __noinline__ double delta_s_fp64(PopArr<L::Q, T> g, double rho0) {
 // its exact dS is then evaluated later from the unchanged source field.
 template <typename L, typename T, int EQ>
 __device__ __forceinline__ bool update_site(const Params& P, T* g, int x, int y, long long t,
-                                            bool& nonfinite, NewtonCount& nc) {
+                                            bool& nonfinite, NewtonCount& nc,
+                                            const float* a0 = nullptr) {
     T gs[L::Q], rho, ux, uy;
-    site_equilibrium<L, T, EQ>(P, g, gs, rho, ux, uy, nc);
+    site_equilibrium<L, T, EQ>(P, g, gs, rho, ux, uy, nc, a0);
     nonfinite |= !isfinite(rho + ux + uy);
     if (x == P.probe_x && y == P.probe_y && P.probe_ring)
         P.probe_ring[t % P.ring_cap] = (double)ux;
@@ -168,6 +185,34 @@ __device__ __forceinline__ bool update_site(const Params& P, T* g, int x, int y,
     for (int i = 0; i < L::Q; i++) g[i] = dfma<T>(nb2, d[i], g[i]);
     return pending;
 }
+
+// Learned form: the network's Newton start point for the warp's 32 sites
+// (lane l: its gathered site g, or valid = false).  Every lane must call it.
+template <typename T>
+__device__ __forceinline__ void mlp_site_start(const Params& P, const MlpSmem& ms, bool valid,
+                                               const T* g, float* a) {
+    float rho = 1.0f, ux = 0.0f, uy = 0.0f, e2 = 0.0f;
+    if (valid) {
+        T drho, r, jx, jy;
+        moments<D2Q9, T>(g, Par<T>::rho0(P), drho, r, jx, jy);
+        rho = (float)r;
+        const float ir = 1.0f / rho;
+        ux = (float)jx * ir;
+        uy = (float)jy * ir;
+        e2 = (float)energy_moment<D2Q9, T>(g, Par<T>::rho0(P));
+        valid = rho > 0.0f && isfinite(rho + ux + uy + e2);
+    }
+    mlp_warm_start(ms, valid, rho, ux, uy, e2, a);
+}
+
+// Shared copy of the network in the learned form's kernels (empty otherwise).
+template <int EQ> struct MlpSlot {
+    __device__ void fill(const Params&) {}
+};
+template <> struct MlpSlot<EQ_ENERGY_MLP> {
+    MlpSmem s;
+    __device__ void fill(const Params& P) { mlp_fill(s, P.mlp); }
+};
 
 // Exact dS of site (x, y) from the source field (the pre-collision state is
 // re-gathered; the source is not written during a step).  The precision
@@ -544,8 +589,10 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_collide_d2q9(const __grid_
     using T = typename Store<S>::T;
     constexpr int TX = 32 * VEC;
     __shared__ FinishShared fs;
+    __shared__ MlpSlot<EQ> mslot;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) fs.npend = 0;
+    mslot.fill(P);
     __syncthreads();
     const long long t = *P.step;
     const S* __restrict__ src = static_cast<const S*>(P.src);
@@ -595,7 +642,16 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_collide_d2q9(const __grid_
             }
             bool pend[VEC];
 #pragma unroll
-            for (int s = 0; s < VEC; s++) pend[s] = update_site<L, T, EQ>(P, g[s], xs + s, y, t, nonfinite, nc);
+            for (int s = 0; s < VEC; s++) {
+                if constexpr (EQ == EQ_ENERGY_MLP) {
+                    // interior tile: every lane holds a fluid site
+                    float a0[3];
+                    mlp_site_start<T>(P, mslot.s, true, g[s], a0);
+                    pend[s] = update_site<L, T, EQ>(P, g[s], xs + s, y, t, nonfinite, nc, a0);
+                } else {
+                    pend[s] = update_site<L, T, EQ>(P, g[s], xs + s, y, t, nonfinite, nc);
+                }
+            }
 #pragma unroll
             for (int i = 0; i < L::Q; i++) {
                 T v[VEC];
@@ -699,9 +755,10 @@ struct TmaShared {
     int tile[8];   // tile held by each stage (-1: none left)
 };
 
-template <typename S, int R, int STAGES>
+template <typename S, int R, int STAGES, int EQ>
 constexpr size_t tma_smem_bytes() {
-    return 128 + (size_t)STAGES * TmaLayout<S, R>::STAGE_BYTES + 8 * STAGES + sizeof(TmaShared) + 16;
+    return 128 + (size_t)STAGES * TmaLayout<S, R>::STAGE_BYTES + 8 * STAGES + sizeof(TmaShared) + 16 +
+           (EQ == EQ_ENERGY_MLP ? sizeof(MlpSlot<EQ>) + 16 : 0);
 }
 
 // Pre-collision deviations of site (x, y) of a staged tile, from shared
@@ -776,6 +833,8 @@ __global__ void __launch_bounds__(32 * R, 16 / R)
     S* stages = reinterpret_cast<S*>(smem);
     unsigned long long* full = reinterpret_cast<unsigned long long*>(smem + STAGES * LY::STAGE_BYTES);
     TmaShared& sh = *reinterpret_cast<TmaShared*>(smem + STAGES * LY::STAGE_BYTES + 8 * STAGES);
+    constexpr size_t kMlpOff = (STAGES * LY::STAGE_BYTES + 8 * STAGES + sizeof(TmaShared) + 15) / 16 * 16;
+    MlpSlot<EQ>& mslot = *reinterpret_cast<MlpSlot<EQ>*>(smem + kMlpOff);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
         for (int st = 0; st < STAGES; st++) mbar_init(&full[st], 1);
@@ -783,6 +842,7 @@ __global__ void __launch_bounds__(32 * R, 16 / R)
         sh.npend = 0;
         sh.abort = 0;
     }
+    mslot.fill(P);
     __syncthreads();
     const long long t = *P.step;
     S* __restrict__ dst = static_cast<S*>(P.dst);
@@ -852,7 +912,10 @@ __global__ void __launch_bounds__(32 * R, 16 / R)
         for (int s = 0; s < TX / 32; s++) {
             const int x = x0 + lane + 32 * s;
             bool pend = false;
-            if (x < P.nx && y < P.ny) {
+            // the learned form enters with every lane (its warm start is a
+            // warp-wide evaluation); lanes outside the grid then carry no site
+            if (EQ == EQ_ENERGY_MLP || (x < P.nx && y < P.ny)) {
+                const bool inside = x < P.nx && y < P.ny;
                 const int c = x - x0;
                 const int o = y * nxp + x;
                 bool shift = clean;
@@ -863,8 +926,11 @@ __global__ void __launch_bounds__(32 * R, 16 / R)
                             !near_obstacle;
                 }
                 T g[L::Q];
-                bool fluid = true;
-                if (shift) {
+                bool fluid = inside;
+                if (!inside) {
+#pragma unroll
+                    for (int i = 0; i < L::Q; i++) g[i] = T(0);
+                } else if (shift) {
 #pragma unroll
                     for (int i = 0; i < L::Q; i++)
                         g[i] = Store<S>::load(sb + i * LY::PLANE + c - L::cx(i) - L::cy(i) * LY::W, 0);
@@ -877,13 +943,33 @@ __global__ void __launch_bounds__(32 * R, 16 / R)
                 } else {
                     gather_site_smem<S, R>(P, box, x0, y0, x, y, g);
                 }
-                if (fluid) pend = update_site<L, T, EQ>(P, g, x, y, t, nonfinite, nc);
+                if constexpr (EQ == EQ_ENERGY_MLP) {
+                    float a0[3];
+                    __syncwarp();
+                    mlp_site_start<T>(P, mslot.s, fluid, g, a0);
+                    if (fluid) pend = update_site<L, T, EQ>(P, g, x, y, t, nonfinite, nc, a0);
+                } else {
+                    if (fluid) pend = update_site<L, T, EQ>(P, g, x, y, t, nonfinite, nc);
+                }
+                if (inside) {
 #pragma unroll
-                for (int i = 0; i < L::Q; i++) Store<S>::store(dst + i * plane + o, 0, g[i]);
+                    for (int i = 0; i < L::Q; i++) Store<S>::store(dst + i * plane + o, 0, g[i]);
+                }
             }
             warp_pend(P, sh.pend, &sh.npend, pend, (unsigned)(y * P.nx + x));
         }
         __syncthreads();
+        // resolve the block's pending sites once its list could not take
+        // another tile's, so that none overflow to the global list (which the
+        // last block alone would resolve).  npend is read between two
+        // barriers with no writes to it in between: the branch is uniform.
+        if (sh.npend > (unsigned)(kPend - TX * R)) {
+            resolve_list<L, S, EQ>(P, (int)min(sh.npend, (unsigned)kPend),
+                                   [&](int j) { return sh.pend[j]; });
+            __syncthreads();
+            if (threadIdx.x == 0) sh.npend = 0;
+            __syncthreads();
+        }
     }
     __syncthreads();
     if (sh.abort && threadIdx.x == 0) {
@@ -1077,7 +1163,7 @@ cudaError_t occupancy_d2q9(int* per_sm) {
 
 template <typename S, int EQ, int R, int STAGES>
 cudaError_t launch_d2q9_tma(const Params& P, const void* tmap, cudaStream_t st) {
-    constexpr size_t smem = tma_smem_bytes<S, R, STAGES>();
+    constexpr size_t smem = tma_smem_bytes<S, R, STAGES, EQ>();
     const long long tiles = (long long)((P.nx + kTmaTX - 1) / kTmaTX) * ((P.ny + R - 1) / R);
     const long long want = (tiles + 3) / 4;   // at least 4 tiles per block
     const unsigned blocks = (unsigned)std::max(1ll, std::min(want, (long long)P.grid_blocks));
@@ -1088,7 +1174,7 @@ cudaError_t launch_d2q9_tma(const Params& P, const void* tmap, cudaStream_t st) 
 
 template <typename S, int EQ, int R, int STAGES>
 cudaError_t setup_d2q9_tma(int* per_sm) {
-    constexpr size_t smem = tma_smem_bytes<S, R, STAGES>();
+    constexpr size_t smem = tma_smem_bytes<S, R, STAGES, EQ>();
     cudaError_t e = cudaFuncSetAttribute(k_collide_d2q9_tma<S, EQ, R, STAGES>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -47,7 +47,8 @@ class SplitMix64:
 # --------------------------------------------------------------------------
 BC_BB, BC_FREESLIP, BC_INLET, BC_OUTLET, BC_PERIODIC = 0, 1, 2, 3, 4
 D1Q3, D2Q9 = 0, 1
-EQ_POLY, EQ_ENTROPIC, EQ_ENERGY = 0, 1, 2
+EQ_POLY, EQ_ENTROPIC, EQ_ENERGY, EQ_ENERGY_MLP = 0, 1, 2, 3
+SEED_ENERGY_SAMPLES = 20070531
 
 
 @dataclass
@@ -186,6 +187,30 @@ def workload_c5(nruns=64, seed=SEED_CYLINDER):
                      seed=seed + r + 1)
         runs.append(w)
     return runs
+
+
+def energy_factor(w, smooth=True, amplitude=0.1, seed=SEED_CYLINDER):
+    """Factor applied to the isothermal energy of the initial field of the
+    energy-constrained runs: 1 + a sin(2 pi y / ny) cos(2 pi x / nx) (a
+    smooth temperature pattern), or 1 + a U[-1, 1] per site."""
+    if not smooth:
+        return 1.0 + amplitude * uniform(seed, (w.ny, w.nx))
+    y = np.arange(w.ny)[:, None]
+    x = np.arange(w.nx)[None, :]
+    return 1.0 + amplitude * np.sin(2 * np.pi * y / w.ny) * np.cos(2 * np.pi * x / w.nx)
+
+
+def energy_samples(seed, n, rho=(0.5, 2.0), u_max=0.2, escale=(0.9, 1.1)):
+    """Moments for the learned form's training set: rho ~ U[rho], u uniform
+    in the disc |u| < u_max, and an energy factor ~ U[escale] that multiplies
+    the isothermal energy 2E(rho, u).  Returns (rho, ux, uy, escale)."""
+    g = SplitMix64(seed)
+    u = g.uniform(4 * n).reshape(4, n)
+    r = rho[0] + (rho[1] - rho[0]) * u[0]
+    rad = u_max * np.sqrt(u[1])
+    ang = 2.0 * np.pi * u[2]
+    es = escale[0] + (escale[1] - escale[0]) * u[3]
+    return r, rad * np.cos(ang), rad * np.sin(ang), es
 
 
 # Generic random arrays for parity tests -----------------------------------

@@ -76,6 +76,13 @@ def load(path=None):
         "lb_info": ([H, vp, vp], ip),
         "lb_set_tile_shape": ([H, ip], ip),
         "lb_select_only_noalloc": ([vp, ip, dp, ip, vp, vp, vp], ip),
+        "lb_mlp_init": ([vp, ip, C.c_ulonglong], ip),
+        "lb_energy_dataset": ([vp, vp, vp, vp, C.c_longlong, vp, vp, vp, vp, vp], ip),
+        "lb_mlp_normalise": ([vp, vp, vp, C.c_longlong, vp], ip),
+        "lb_mlp_forward": ([vp, vp, C.c_longlong, vp, vp], ip),
+        "lb_mlp_grad": ([vp, vp, vp, ip, vp, vp, vp], ip),
+        "lb_mlp_adam": ([vp, vp, vp, vp, C.c_longlong, dp, vp], ip),
+        "lb_mlp_train": ([vp, vp, vp, C.c_longlong, ip, ip, dp, dp, vp, vp], ip),
         "lb_last_error": ([], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -143,6 +150,48 @@ def mlp_param_count():
     return load().lb_mlp_param_count()
 
 
+# Learned form (device pointers are integers, streams cudaStream_t integers
+# or None; every call is asynchronous on its stream) ----------------------
+
+def _vp(x):
+    return C.c_void_p(x) if x else None
+
+
+def mlp_init(seed):
+    """Initial parameters (host FP32 array), lb_mlp_init."""
+    L = load()
+    p = np.zeros(L.lb_mlp_param_count(), np.float32)
+    _check(L.lb_mlp_init(_ptr(p), p.size, int(seed) & ((1 << 64) - 1)))
+    return p
+
+
+def energy_dataset(rho, ux, uy, escale, n, feat, dmu, mu=None, stats=None, stream=None):
+    _check(load().lb_energy_dataset(_vp(rho), _vp(ux), _vp(uy), _vp(escale), int(n), _vp(feat),
+                                    _vp(dmu), _vp(mu), _vp(stats), _vp(stream)))
+
+
+def mlp_normalise(params, feat, dmu, n, stream=None):
+    _check(load().lb_mlp_normalise(_vp(params), _vp(feat), _vp(dmu), int(n), _vp(stream)))
+
+
+def mlp_forward(params, feat, n, y, stream=None):
+    _check(load().lb_mlp_forward(_vp(params), _vp(feat), int(n), _vp(y), _vp(stream)))
+
+
+def mlp_grad(params, feat, dmu, n, grad, loss=None, stream=None):
+    _check(load().lb_mlp_grad(_vp(params), _vp(feat), _vp(dmu), int(n), _vp(grad), _vp(loss),
+                              _vp(stream)))
+
+
+def mlp_adam(params, grad, m, v, t, lr, stream=None):
+    _check(load().lb_mlp_adam(_vp(params), _vp(grad), _vp(m), _vp(v), int(t), float(lr), _vp(stream)))
+
+
+def mlp_train(params, feat, dmu, n, batch, epochs, lr0, lr1, loss_log=None, stream=None):
+    _check(load().lb_mlp_train(_vp(params), _vp(feat), _vp(dmu), int(n), int(batch), int(epochs),
+                               float(lr0), float(lr1), _vp(loss_log), _vp(stream)))
+
+
 class Lattice:
     """One run (a lb_handle).  Mirrors the C calls one to one."""
 
@@ -161,10 +210,11 @@ class Lattice:
     @classmethod
     def from_workload(cls, w, precision=LB_F32, stream=None, **over):
         """Create from a paper_0705_4371_gb300.inputs.Workload."""
-        p = dict(nu=w.nu, delta=w.delta, k=w.k)
+        p = dict(nu=w.nu, delta=w.delta, k=w.k, equilibrium=w.eq)
         p.update(over)
         bc = boundaries(w.bc, w.rho_in, w.u_in, w.obstacle)
-        return cls(w.lattice, w.nx, w.ny, w.eq, p["nu"], p["delta"], p["k"], bc, precision, stream)
+        return cls(w.lattice, w.nx, w.ny, p["equilibrium"], p["nu"], p["delta"], p["k"], bc, precision,
+                   stream)
 
     def close(self):
         if getattr(self, "h", None):

@@ -58,3 +58,21 @@ def moment_errors(got, ref, mask, u_ref):
     e_rho = float(np.abs(rg[f] - ro[f]).max() / np.abs(ro[f]).max())
     e_u = float(max(np.abs(ug[f] - uo[f]).max(), np.abs(vg[f] - vo[f]).max()) / u_ref)
     return e_M, e_rho, e_u
+
+
+def mlp_random_params(seed, scale=0.5):
+    """Network parameters for parity tests: uniform weights and biases, the
+    normalisation of the learned form's sample distribution."""
+    from oracle import mlp
+    u = inputs.uniform(seed, (mlp.N_PARAMS,)) * scale
+    d = mlp.unpack(u)
+    d["mean"] = np.array([1.25, 0.0, 0.0, 0.66])
+    d["inv_std"] = np.array([2.3, 10.0, 10.0, 30.0])
+    d["out_scale"] = np.array([0.05, 0.02, 0.02, 0.1])
+    return mlp.pack(d).astype(np.float32).astype(np.float64)
+
+
+def mlp_random_features(seed, n):
+    rho, ux, uy, es = inputs.energy_samples(seed, n)
+    th = (2.0 / 3.0) * es + 0.01 * inputs.uniform(seed + 1, (n,))
+    return np.stack([rho, ux, uy, th], axis=1).astype(np.float32).astype(np.float64)
