@@ -286,6 +286,8 @@ def run_gpu(args):
 
     if args.forms and args.learned and rank == 0:
         forms["learned"] = learned_form(args, stream)
+    if args.forms and args.batched and rank == 0:
+        forms["batched"] = batched_form(args, stream, peaks)
 
     cpu = cpu_baseline(w, args) if (rank == 0 and world == 1 and not args.no_cpu) else None
     clk = clocks.summary()
@@ -369,6 +371,64 @@ def learned_form(args, stream):
                          "newton_fp64_it_per_site": round(it64 / max(sites, 1), 4),
                          "newton_fails": int(fails), "steps": args.learned_steps}
     out["speedup"] = round(out["mlp_warm_start"]["MLUPS"] / out["newton"]["MLUPS"], 4)
+    return out
+
+
+def batched_form(args, stream, peaks):
+    """64 cylinder runs (sizes 256 x 128 .. 2048 x 1024, Re, delta and k
+    drawn per run, seeded) in FP32 deviation storage: aggregate MLUPS of the
+    batched launches (one launch per step covers every run; graphs of 32)
+    against the same runs stepped one after another (each through its own
+    graphs), the autotuner's choice, and the batched kernel's bandwidth."""
+    import tempfile
+    import torch
+    from paper_0705_4371_gb300 import lbm
+    ws = inputs.workload_c5()
+    out = {"workload": "64 cylinder runs (c5 recipe, seed %d)" % inputs.SEED_CYLINDER, "storage": "f32dev"}
+    with lbm.Batch(ws, precision=lbm.LB_F32_DEV, stream=stream.cuda_stream) as b:
+        for r, w in enumerate(ws):
+            b.run(r).init_equilibrium(*inputs.cylinder_fields(w))
+        b.step(args.batch_spinup)
+        b.sync()
+        cache = args.autotune_cache or os.path.join(tempfile.gettempdir(), "lbm_gb300_autotune.json")
+        t0 = time.perf_counter()
+        v = b.autotune(steps=10, cache_path=cache)
+        info = b.info()
+        out.update({"runs": info["runs"], "sites": info["sites"], "tiles": info["tiles"],
+                    "autotuned_variant": v, "tile_rows": info["tile_rows"],
+                    "autotune_s": round(time.perf_counter() - t0, 3)})
+        b.step(32)
+        b.sync()
+
+        def timed(fn, n):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            fn(n)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1)
+
+        n = args.batch_steps
+        ms_b = timed(b.step, n)
+        ms_s = timed(b.step_sequential, n)
+        b.set_timing(True)
+        b.step(20)
+        kt = b.kernel_times(reset=True)
+        b.set_timing(False)
+        b.sync()
+        per = kt["ms"] / max(kt["launches"], 1)
+        bytes_site = 72
+        ach = bytes_site * info["sites"] / (per * 1e-3) / 1e9
+        out.update({
+            "batched": {"MLUPS": round(info["sites"] * n / (ms_b * 1e-3) / 1e6, 1),
+                        "ms_per_step": round(ms_b / n, 4), "launches_per_step": 1},
+            "sequential": {"MLUPS": round(info["sites"] * n / (ms_s * 1e-3) / 1e6, 1),
+                           "ms_per_step": round(ms_s / n, 4), "launches_per_step": len(ws)},
+            "speedup": round(ms_s / ms_b, 3), "steps": n,
+            "kernel": {"name": "k_collide_batch", "avg_launch_ms": round(per, 5),
+                       "algorithmic_bytes_per_site": bytes_site, "achieved_GBps": round(ach, 1),
+                       "frac": round(ach / peaks["hbm_gbs"], 4)}})
     return out
 
 
@@ -460,6 +520,10 @@ def main():
     ap.add_argument("--forms", type=int, default=1)
     ap.add_argument("--form-steps", type=int, default=2000)
     ap.add_argument("--learned", type=int, default=1)
+    ap.add_argument("--batched", type=int, default=1)
+    ap.add_argument("--batch-steps", type=int, default=400)
+    ap.add_argument("--batch-spinup", type=int, default=64)
+    ap.add_argument("--autotune-cache", default="")
     ap.add_argument("--learned-steps", type=int, default=400)
     ap.add_argument("--learned-warmup", type=int, default=20)
     ap.add_argument("--mlp-samples", type=int, default=10_000_000)

@@ -318,6 +318,69 @@ int lb_info(lb_handle* h, long long* out, double* beta_out);
 /* Thread-local message of the last failed call ("" if none). */
 const char* lb_last_error(void);
 
+/* ---- Batched form ------------------------------------------------------
+ * Many independent D2Q9 runs (each one the method of Sec. 3.2 on its own
+ * grid) advanced together: one kernel launch per time step covers the block
+ * tiles of every run (a flat tile list taken by a persistent grid), and the
+ * block that finishes a run's last tile performs that run's selection and
+ * Ehrenfests' step.  Steps are replayed as CUDA graphs of 32.  Results are
+ * bit-identical to stepping each run alone with lb_step.  The paper runs
+ * one flow at a time; the batch is this implementation's way to fill the
+ * GPU with small runs (parameter sweeps). */
+typedef struct lb_run_desc {
+    int lattice;            /* LB_D2Q9 */
+    int nx, ny;
+    int equilibrium;        /* LB_EQ_POLY or LB_EQ_ENTROPIC, the same for every run */
+    double nu, delta;
+    int k;
+    lb_boundaries bc;
+    int precision;          /* the same for every run */
+} lb_run_desc;
+
+typedef struct lb_batch lb_batch;
+
+/* Creates the runs (as lb_create would, on one stream: cuda_stream, or a
+ * new one when NULL).  Fails with LB_ERR_ARG for other lattices or
+ * equilibria, mixed precisions or equilibria, or more than 4096 runs. */
+int lb_batch_create(const lb_run_desc* runs, int nruns, void* cuda_stream, lb_batch** out);
+void lb_batch_destroy(lb_batch* b);
+
+/* The run r of the batch (owned by the batch; NULL if out of range): use it
+ * to initialise, read and log the run.  Stepping it alone with lb_step
+ * makes the next lb_batch_step fail with LB_ERR_STATE. */
+lb_handle* lb_batch_run(lb_batch* b, int r);
+
+/* Advances every run by n steps (batched launches).  Asynchronous; errors
+ * of the runs are reported by the next call, as for lb_step. */
+int lb_batch_step(lb_batch* b, int n);
+
+/* The same n steps through each run's own lb_step, one run after another
+ * (the baseline the batched launches are measured against). */
+int lb_batch_step_sequential(lb_batch* b, int n);
+
+int lb_batch_sync(lb_batch* b);
+
+/* Tile variant of the batched kernel: 0 = 8-row tiles, 2 stages; 1 =
+ * 4-row tiles, 3 stages.  Synchronises. */
+int lb_batch_set_variant(lb_batch* b, int variant);
+
+/* Autotuner: when cache_path (may be NULL) holds an entry for this device
+ * and batch (device name, SM count, storage, equilibrium, run sizes), its
+ * variant is used; otherwise every variant is timed over `steps` steps
+ * (CUDA events), the fastest is chosen and written to the cache (a JSON
+ * object).  Timing advances every run by 1 + variants x (steps + 2) steps
+ * (all variants compute identical results).  variant_out may be NULL. */
+int lb_batch_autotune(lb_batch* b, int steps, const char* cache_path, int* variant_out);
+
+/* Per-launch CUDA events (graphs are not used while enabled), summed by
+ * lb_batch_kernel_times (synchronises). */
+int lb_batch_set_timing(lb_batch* b, int enable);
+int lb_batch_kernel_times(lb_batch* b, double* ms, long long* launches, int reset);
+
+/* out[8]: runs, sites, tiles, grid blocks, blocks per SM, variant, tile
+ * rows, steps per graph. */
+int lb_batch_info(lb_batch* b, long long* out);
+
 #ifdef __cplusplus
 }
 #endif

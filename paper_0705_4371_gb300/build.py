@@ -17,7 +17,8 @@ HEADERS = [os.path.join(ROOT, "include", "lbm.h")]
 
 SOURCES = ["lbm_kernels_f64.cu", "lbm_kernels_f32.cu", "lbm_kernels_f16.cu",
            "lbm_energy_f64.cu", "lbm_energy_f32.cu", "lbm_energy_f16.cu",
-           "lbm_api.cu", "lbm_noalloc.cu", "lbm_mlp.cu"]
+           "lbm_api.cu", "lbm_noalloc.cu", "lbm_mlp.cu",
+           "lbm_batch.cu", "lbm_batch_f64.cu", "lbm_batch_f32.cu", "lbm_batch_f16.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -fmad=false: no automatic multiply-add contraction; the kernels write their

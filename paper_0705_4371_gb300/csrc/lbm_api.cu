@@ -230,13 +230,11 @@ int build_graph(lb_handle* h, int start) {
 
 bool valid_kind(int k) { return k >= LB_BB && k <= LB_PERIODIC; }
 
-// Tensor maps describing each population buffer as a 3-D array
-// (x: nx, y: ny, plane: Q) for the staged tile shapes: box = (128 + 2 H)
-// x (R + 2) x 1 elements, H = 16 bytes of halo on each side and one row
-// above and below; coordinates outside the array read as zero.
-int make_tensor_maps(lb_handle* h) {
-    const int rows = staged_rows(h->tile_shape);
-    if (h->lattice != LB_D2Q9 || rows == 0) return LB_OK;
+// Tensor map describing population buffer b as a 3-D array (x: nx, y: ny,
+// plane: Q) for staged tiles of R = rows rows: box = (128 + 2 H) x (R + 2)
+// x 1 elements, H = 16 bytes of halo on each side and one row above and
+// below; coordinates outside the array read as zero.
+int encode_tensor_map(const lb_handle* h, int b, int rows, CUtensorMap* out) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
         void* fn = nullptr;
@@ -255,11 +253,19 @@ int make_tensor_maps(lb_handle* h) {
     const cuuint64_t gstride[2] = {(cuuint64_t)h->nxp * es, (cuuint64_t)h->plane * es};
     const cuuint32_t box[3] = {(cuuint32_t)(128 + 2 * (16 / es)), (cuuint32_t)(rows + 2), 1};
     const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = encode(out, dt, 3, h->buf[b], gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(LB_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return LB_OK;
+}
+
+int make_tensor_maps(lb_handle* h) {
+    const int rows = staged_rows(h->tile_shape);
+    if (h->lattice != LB_D2Q9 || rows == 0) return LB_OK;
     for (int b = 0; b < 2; b++) {
-        CUresult r = encode(&h->tmap[b], dt, 3, h->buf[b], gdim, gstride, box, estr,
-                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) return fail(LB_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+        const int rc = encode_tensor_map(h, b, rows, &h->tmap[b]);
+        if (rc != LB_OK) return rc;
     }
     return LB_OK;
 }
@@ -277,6 +283,46 @@ int size_grid(lb_handle* h) {
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------------------
+// What the batched form (lbm_batch.cu) needs of a run.
+// ---------------------------------------------------------------------------
+namespace lbm {
+
+RunView run_view(const lb_handle* h) {
+    RunView v;
+    v.lattice = h->lattice;
+    v.nx = h->nx;
+    v.ny = h->ny;
+    v.eq = h->eq;
+    v.prec = h->prec;
+    v.cur = h->cur;
+    v.prestream = h->prestream;
+    v.replaying = h->replay_n > 0 && h->h_step < h->replay_t0 + h->replay_n;
+    v.step = h->h_step;
+    v.stream = h->stream;
+    return v;
+}
+
+Params run_params(const lb_handle* h, int src, bool prestream) { return make_params(h, src, prestream); }
+
+int run_tensor_map(const lb_handle* h, int buf, int rows, CUtensorMap* out) {
+    return encode_tensor_map(h, buf, rows, out);
+}
+
+void run_advance(lb_handle* h, long long n) {
+    h->h_step += n;
+    if (n & 1) h->cur = 1 - h->cur;
+    if (n > 0) h->prestream = false;
+}
+
+int run_check(lb_handle* h) { return check_sticky(h, false); }
+
+int run_queue_err(lb_handle* h) { return queue_err_readback(h); }
+
+int run_fail(int code, const char* msg) { return fail(code, "%s", msg); }
+
+}  // namespace lbm
 
 extern "C" {
 

@@ -1,0 +1,218 @@
+// lbm_batch_kernels.cuh -- the batched form: one launch advances every run
+// of a batch by one time step.
+//
+// The runs' block tiles (R rows x 128 sites, staged in shared memory by
+// bulk tensor copies exactly as in the single-run staged kernel) form one
+// flat list; a persistent grid takes tiles from a global counter, so small
+// and large runs share the GPU without idle tails per run.  A tile's sites
+// go through the same per-site update as a single run (tma_tile), its
+// pending sites are resolved before the tile is counted as done, and the
+// block that finishes a run's last tile runs that run's selection and
+// Ehrenfests' step (Sec. 3.2) while the other blocks go on with other runs'
+// tiles.  The counters of a step are selected by its buffer parity; the
+// last run to finish resets those of the next step.
+#pragma once
+
+#include "lbm_internal.h"
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+
+constexpr int kBatchStage = 512;   // candidates a select stages in shared memory
+constexpr int kBatchSmemRuns = 256;   // tile bases kept in shared memory (more runs: global)
+
+// Release (or acquire-release) add at device scope: publishes the block's
+// writes, which a barrier made the calling thread observe, with the count.
+__device__ __forceinline__ unsigned atomic_add_release(unsigned* p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.release.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+struct BatchShared {
+    SelectShared ss;
+    // pending sites of the tile being computed; between tiles, the
+    // candidate staging of a run's selection (keys, then indices)
+    alignas(16) unsigned pend[kPend];
+    unsigned npend;
+    int abort;
+    int tile[4], run[4];   // per stage: tile index within its run (-1: none left), run
+    int base[kBatchSmemRuns + 1];   // first tile of each run (batches of up to kBatchSmemRuns runs)
+};
+static_assert(kBatchStage * (sizeof(unsigned long long) + sizeof(unsigned)) <= sizeof(unsigned) * kPend,
+              "candidate staging must fit in the pending list");
+static_assert(sizeof(Params) % 8 == 0, "Params is copied in 8-byte words");
+
+template <typename S, int R, int STAGES>
+constexpr size_t batch_params_offset() {
+    return ((size_t)STAGES * TmaLayout<S, R>::STAGE_BYTES + 8 * STAGES + sizeof(BatchShared) + 15) / 16 * 16;
+}
+
+template <typename S, int R, int STAGES>
+constexpr size_t batch_smem_bytes() {
+    return 128 + batch_params_offset<S, R, STAGES>() + (size_t)STAGES * sizeof(Params);
+}
+
+template <typename S, int EQ, int R, int STAGES>
+__global__ void __launch_bounds__(32 * R, 16 / R) k_collide_batch(const __grid_constant__ BatchArgs A) {
+    using L = D2Q9;
+    using LY = TmaLayout<S, R>;
+    constexpr int TX = kTmaTX;
+    static_assert(STAGES <= 4, "at most 4 stages");
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
+    S* stages = reinterpret_cast<S*>(smem);
+    unsigned long long* full = reinterpret_cast<unsigned long long*>(smem + STAGES * LY::STAGE_BYTES);
+    BatchShared& sh = *reinterpret_cast<BatchShared*>(smem + STAGES * LY::STAGE_BYTES + 8 * STAGES);
+    Params* sp = reinterpret_cast<Params*>(smem + batch_params_offset<S, R, STAGES>());
+    MlpSlot<EQ> mslot;   // empty: the batch runs the polynomial and entropic forms
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < STAGES; st++) mbar_init(&full[st], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        sh.npend = 0;
+        sh.abort = 0;
+    }
+    const bool base_in_smem = A.nruns <= kBatchSmemRuns;
+    if (base_in_smem)
+        for (int q = threadIdx.x; q <= A.nruns; q += blockDim.x) sh.base[q] = A.tile_base[q];
+    __syncthreads();
+    const int* tile_base = base_in_smem ? sh.base : A.tile_base;
+    int run_hint = 0;   // tiles are claimed in increasing order: runs only move forward
+
+    // Thread 0 claims the next tile, copies its run's parameters into the
+    // stage's slot and issues the copies; the stage's mbarrier publishes
+    // both (-1: no tile left; the phase then completes by a plain arrive).
+    auto fill = [&](int st) {
+        unsigned long long* bar = &full[st];
+        const int tile = (int)atomicAdd(A.tile_counter, 1u);
+        if (tile >= A.total_tiles) {
+            sh.tile[st] = -1;
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+            return;
+        }
+        int lo = run_hint;   // the last run whose first tile is <= tile
+        while (tile_base[lo + 1] <= tile) lo++;
+        run_hint = lo;
+        const unsigned long long* src = reinterpret_cast<const unsigned long long*>(A.P + lo);
+        unsigned long long* dst = reinterpret_cast<unsigned long long*>(sp + st);
+        unsigned long long w[sizeof(Params) / 8];
+#pragma unroll
+        for (int k = 0; k < (int)(sizeof(Params) / 8); k++) w[k] = __ldg(src + k);
+#pragma unroll
+        for (int k = 0; k < (int)(sizeof(Params) / 8); k++) dst[k] = w[k];
+        const int lt = tile - tile_base[lo];
+        sh.tile[st] = lt;
+        sh.run[st] = lo;
+        const int tiles_x = (sp[st].nx + TX - 1) / TX;
+        const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
+        mbar_expect_tx(bar, (unsigned)LY::TX_BYTES);
+        S* base = stages + (size_t)st * (LY::STAGE_BYTES / sizeof(S));
+#pragma unroll
+        for (int i = 0; i < L::Q; i++)
+            tma_load_3d(base + i * LY::PLANE, A.tm + lo, tx * TX - LY::H, ty * R - 1, i, bar);
+    };
+    if (threadIdx.x == 0)
+        for (int st = 0; st < STAGES - 1; st++) fill(st);
+    int jj = 0;
+    for (;; jj++) {
+        const int st = jj % STAGES;
+        const unsigned parity = (unsigned)((jj / STAGES) & 1);
+        if (__syncthreads_or(!mbar_wait(&full[st], parity))) {
+            if (threadIdx.x == 0) {
+                for (int q = 0; q < A.nruns; q++) atomicOr(A.P[q].err, ERR_TIMEOUT);
+                sh.abort = 1;
+            }
+            break;
+        }
+        const int lt = sh.tile[st];
+        if (lt < 0) break;
+        const int r = sh.run[st];
+        if (threadIdx.x == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            fill((jj + STAGES - 1) % STAGES);
+        }
+        const Params& P = sp[st];
+        const int tiles_x = (P.nx + TX - 1) / TX;
+        const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
+        const long long t = __ldcg(P.step);
+        bool nonfinite = false;
+        NewtonCount nc = {0, 0, 0, 0};
+        const S* box = stages + (size_t)st * (LY::STAGE_BYTES / sizeof(S));
+        tma_tile<S, EQ, R>(P, box, tx * TX, ty * R, t, sh.pend, &sh.npend, mslot, nonfinite, nc);
+        const int nf = __syncthreads_or(nonfinite);
+        // the tile's pending sites (npend is read between barriers: uniform)
+        if (sh.npend > 0) {
+            resolve_list<L, S, EQ>(P, (int)min(sh.npend, (unsigned)kPend), [&](int j) { return sh.pend[j]; });
+            __syncthreads();
+            if (threadIdx.x == 0) sh.npend = 0;
+        }
+        // the barrier above made the tile's writes visible to thread 0; its
+        // release add publishes them with the count.  The run's last tile
+        // acquires every other tile's writes before the selection.
+        int sel = 0;
+        if (threadIdx.x == 0) {
+            if (nf) atomicOr(P.err, ERR_NONFINITE);
+            const unsigned done = atomic_add_release(A.tiles_done + r, 1u) + 1u;
+            sel = done == (unsigned)(tile_base[r + 1] - tile_base[r]);
+            if (sel) __threadfence();
+        }
+        if (__syncthreads_or(sel)) {
+            // every tile of run r is done: its selection and Ehrenfests' step
+            unsigned long long* skey = reinterpret_cast<unsigned long long*>(sh.pend);
+            unsigned* sidx = sh.pend + 2 * kBatchStage;
+            select_and_fix<L, S, EQ>(P, sh.ss, skey, sidx, kBatchStage, 0);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                const unsigned rd = atomicAdd(A.runs_done, 1u) + 1u;
+                if (rd == (unsigned)A.nruns) {
+                    *A.next_tile_counter = 0u;
+                    *A.next_runs_done = 0u;
+                    for (int q = 0; q < A.nruns; q++) A.next_tiles_done[q] = 0u;
+                    __threadfence();
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (sh.abort && threadIdx.x == 0) {
+        // wait (bounded) for copies still in flight into every stage
+        for (int k2 = 0; k2 < STAGES; k2++) {
+            const int j2 = jj + k2;
+            mbar_wait(&full[j2 % STAGES], (unsigned)((j2 / STAGES) & 1));
+        }
+    }
+}
+
+template <typename S, int EQ, int R, int STAGES>
+cudaError_t launch_batch(const BatchArgs& A, int grid, cudaStream_t st) {
+    k_collide_batch<S, EQ, R, STAGES><<<grid, 32 * R, batch_smem_bytes<S, R, STAGES>(), st>>>(A);
+    return cudaGetLastError();
+}
+
+template <typename S, int EQ, int R, int STAGES>
+cudaError_t setup_batch(int* per_sm) {
+    constexpr size_t smem = batch_smem_bytes<S, R, STAGES>();
+    cudaError_t e = cudaFuncSetAttribute(k_collide_batch<S, EQ, R, STAGES>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_collide_batch<S, EQ, R, STAGES>, 32 * R,
+                                                         smem);
+}
+
+template <typename S, int EQ>
+BatchLaunchers batch_launchers_of(int variant) {
+    BatchLaunchers b;
+    if (variant == 1) {
+        b.launch = &launch_batch<S, EQ, 4, 3>;
+        b.setup = &setup_batch<S, EQ, 4, 3>;
+        b.rows = 4;
+    } else {
+        b.launch = &launch_batch<S, EQ, 8, 2>;
+        b.setup = &setup_batch<S, EQ, 8, 2>;
+        b.rows = 8;
+    }
+    return b;
+}
+
+}  // namespace lbm

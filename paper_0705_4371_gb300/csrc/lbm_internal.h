@@ -2,7 +2,10 @@
 // per-storage-type kernel translation units (not part of the public ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
+
+struct lb_handle;
 
 namespace lbm {
 
@@ -39,5 +42,52 @@ void set_last_error(const char* msg);
 
 // select-only test hook: candidates from a device dS array
 cudaError_t launch_emit_from_ds(const Params& P, const double* ds, int n, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// Batched form: many D2Q9 runs advanced by one kernel launch per step.
+// ---------------------------------------------------------------------------
+
+// Arguments of one batched step (device pointers).  The run parameters,
+// tensor maps and counters of a step are selected by its buffer parity.
+struct BatchArgs {
+    const Params* P;               // [nruns] the runs' parameters for this step
+    const CUtensorMap* tm;         // [nruns] tensor maps of the source buffers (64-byte aligned)
+    const int* tile_base;          // [nruns + 1] first tile of each run in the flat tile list
+    int nruns, total_tiles;
+    unsigned* tile_counter;        // this step's tile counter
+    unsigned* tiles_done;          // [nruns] this step's finished tiles per run
+    unsigned* runs_done;           // this step's finished runs
+    unsigned* next_tile_counter;   // the next step's counters, reset by the last run to finish
+    unsigned* next_tiles_done;
+    unsigned* next_runs_done;
+};
+
+struct BatchLaunchers {
+    cudaError_t (*launch)(const BatchArgs&, int grid, cudaStream_t);
+    cudaError_t (*setup)(int* blocks_per_sm);
+    int rows;                      // tile rows (the tile is 128 sites wide)
+};
+
+constexpr int kBatchVariants = 2;  // 0: 8-row tiles, 2 stages; 1: 4-row tiles, 3 stages
+// storage: 0 = FP64, 1 = FP32, 2 = FP16; eq: EQ_POLY or EQ_ENTROPIC
+BatchLaunchers batch_launchers(int storage, int eq, int variant);
+BatchLaunchers batch_launchers_f64(int eq, int variant);
+BatchLaunchers batch_launchers_f32(int eq, int variant);
+BatchLaunchers batch_launchers_f16(int eq, int variant);
+
+// A run as the batch sees it (lbm_api.cu).
+struct RunView {
+    int lattice, nx, ny, eq, prec, cur;
+    bool prestream, replaying;
+    long long step;
+    cudaStream_t stream;
+};
+RunView run_view(const lb_handle* h);
+Params run_params(const lb_handle* h, int src, bool prestream);
+int run_tensor_map(const lb_handle* h, int buf, int rows, CUtensorMap* out);
+void run_advance(lb_handle* h, long long n);
+int run_check(lb_handle* h);
+int run_queue_err(lb_handle* h);
+int run_fail(int code, const char* msg);
 
 }  // namespace lbm

@@ -821,6 +821,80 @@ __device__ __forceinline__ void gather_site_smem(const Params& P, const S* box, 
     }
 }
 
+// One staged tile: rows y0 .. y0 + R - 1 and columns x0 .. x0 + 127 of the
+// run P, from box (the tile's staged source planes); warp w computes row
+// y0 + w, lane l the sites x0 + l + 32 s.  Pending sites (dS not cleared by
+// the bound) are appended to the block's list.
+template <typename S, int EQ, int R>
+__device__ __forceinline__ void tma_tile(const Params& P, const S* box, int x0, int y0, long long t,
+                                         unsigned* pend_list, unsigned* npend, MlpSlot<EQ>& mslot,
+                                         bool& nonfinite, NewtonCount& nc) {
+    using L = D2Q9;
+    using T = typename Store<S>::T;
+    using LY = TmaLayout<S, R>;
+    constexpr int TX = kTmaTX;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    S* __restrict__ dst = static_cast<S*>(P.dst);
+    const int nxp = P.nxp, plane = (int)P.plane;
+    const bool periodic = P.bc[0] == BC_PERIODIC || P.bc[2] == BC_PERIODIC;
+    const int y = y0 + warp;
+    const bool clean = !P.prestream && x0 >= 1 && x0 + TX <= P.nx - 1 && y0 >= 1 &&
+                       y0 + R <= P.ny - 1 &&
+                       (P.ow == 0 || x0 + TX + 1 <= P.ox0 || x0 - 1 >= P.ox0 + P.ow ||
+                        y0 + R + 1 <= P.oy0 || y0 - 1 >= P.oy0 + P.oh);
+    const S* sb = box + (warp + 1) * LY::W + LY::H;
+#pragma unroll 1
+    for (int s = 0; s < TX / 32; s++) {
+        const int x = x0 + lane + 32 * s;
+        bool pend = false;
+        // the learned form enters with every lane (its warm start is a
+        // warp-wide evaluation); lanes outside the grid then carry no site
+        if (EQ == EQ_ENERGY_MLP || (x < P.nx && y < P.ny)) {
+            const bool inside = x < P.nx && y < P.ny;
+            const int c = x - x0;
+            const int o = y * nxp + x;
+            bool shift = clean;
+            if (!shift) {
+                const bool near_obstacle = P.ow > 0 && x >= P.ox0 - 1 && x <= P.ox0 + P.ow &&
+                                           y >= P.oy0 - 1 && y <= P.oy0 + P.oh;
+                shift = !P.prestream && x >= 1 && x <= P.nx - 2 && y >= 1 && y <= P.ny - 2 &&
+                        !near_obstacle;
+            }
+            T g[L::Q];
+            bool fluid = inside;
+            if (!inside) {
+#pragma unroll
+                for (int i = 0; i < L::Q; i++) g[i] = T(0);
+            } else if (shift) {
+#pragma unroll
+                for (int i = 0; i < L::Q; i++)
+                    g[i] = Store<S>::load(sb + i * LY::PLANE + c - L::cx(i) - L::cy(i) * LY::W, 0);
+            } else if (is_solid(P, x, y)) {
+                fluid = false;
+#pragma unroll
+                for (int i = 0; i < L::Q; i++) g[i] = T(0);
+            } else if (periodic) {
+                gather_site<L, S>(P, x, y, g);
+            } else {
+                gather_site_smem<S, R>(P, box, x0, y0, x, y, g);
+            }
+            if constexpr (EQ == EQ_ENERGY_MLP) {
+                float a0[3];
+                __syncwarp();
+                mlp_site_start<T>(P, mslot.s, fluid, g, a0);
+                if (fluid) pend = update_site<L, T, EQ>(P, g, x, y, t, nonfinite, nc, a0);
+            } else {
+                if (fluid) pend = update_site<L, T, EQ>(P, g, x, y, t, nonfinite, nc);
+            }
+            if (inside) {
+#pragma unroll
+                for (int i = 0; i < L::Q; i++) Store<S>::store(dst + i * plane + o, 0, g[i]);
+            }
+        }
+        warp_pend(P, pend_list, npend, pend, (unsigned)(y * P.nx + x));
+    }
+}
+
 template <typename S, int EQ, int R, int STAGES>
 __global__ void __launch_bounds__(32 * R, 16 / R)
     k_collide_d2q9_tma(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap tm) {
@@ -835,7 +909,6 @@ __global__ void __launch_bounds__(32 * R, 16 / R)
     TmaShared& sh = *reinterpret_cast<TmaShared*>(smem + STAGES * LY::STAGE_BYTES + 8 * STAGES);
     constexpr size_t kMlpOff = (STAGES * LY::STAGE_BYTES + 8 * STAGES + sizeof(TmaShared) + 15) / 16 * 16;
     MlpSlot<EQ>& mslot = *reinterpret_cast<MlpSlot<EQ>*>(smem + kMlpOff);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
         for (int st = 0; st < STAGES; st++) mbar_init(&full[st], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -845,9 +918,6 @@ __global__ void __launch_bounds__(32 * R, 16 / R)
     mslot.fill(P);
     __syncthreads();
     const long long t = *P.step;
-    S* __restrict__ dst = static_cast<S*>(P.dst);
-    const int nxp = P.nxp, plane = (int)P.plane;
-    const bool periodic = P.bc[0] == BC_PERIODIC || P.bc[2] == BC_PERIODIC;
     const int tiles_x = (P.nx + TX - 1) / TX;
     const int tiles = tiles_x * ((P.ny + R - 1) / R);
 
@@ -900,64 +970,8 @@ __global__ void __launch_bounds__(32 * R, 16 / R)
             fill((jj + STAGES - 1) % STAGES);
         }
         const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
-        const int x0 = tx * TX, y0 = ty * R;
-        const int y = y0 + warp;
-        const bool clean = !P.prestream && x0 >= 1 && x0 + TX <= P.nx - 1 && y0 >= 1 &&
-                           y0 + R <= P.ny - 1 &&
-                           (P.ow == 0 || x0 + TX + 1 <= P.ox0 || x0 - 1 >= P.ox0 + P.ow ||
-                            y0 + R + 1 <= P.oy0 || y0 - 1 >= P.oy0 + P.oh);
         const S* box = stages + (size_t)st * (LY::STAGE_BYTES / sizeof(S));
-        const S* sb = box + (warp + 1) * LY::W + LY::H;
-#pragma unroll 1
-        for (int s = 0; s < TX / 32; s++) {
-            const int x = x0 + lane + 32 * s;
-            bool pend = false;
-            // the learned form enters with every lane (its warm start is a
-            // warp-wide evaluation); lanes outside the grid then carry no site
-            if (EQ == EQ_ENERGY_MLP || (x < P.nx && y < P.ny)) {
-                const bool inside = x < P.nx && y < P.ny;
-                const int c = x - x0;
-                const int o = y * nxp + x;
-                bool shift = clean;
-                if (!shift) {
-                    const bool near_obstacle = P.ow > 0 && x >= P.ox0 - 1 && x <= P.ox0 + P.ow &&
-                                               y >= P.oy0 - 1 && y <= P.oy0 + P.oh;
-                    shift = !P.prestream && x >= 1 && x <= P.nx - 2 && y >= 1 && y <= P.ny - 2 &&
-                            !near_obstacle;
-                }
-                T g[L::Q];
-                bool fluid = inside;
-                if (!inside) {
-#pragma unroll
-                    for (int i = 0; i < L::Q; i++) g[i] = T(0);
-                } else if (shift) {
-#pragma unroll
-                    for (int i = 0; i < L::Q; i++)
-                        g[i] = Store<S>::load(sb + i * LY::PLANE + c - L::cx(i) - L::cy(i) * LY::W, 0);
-                } else if (is_solid(P, x, y)) {
-                    fluid = false;
-#pragma unroll
-                    for (int i = 0; i < L::Q; i++) g[i] = T(0);
-                } else if (periodic) {
-                    gather_site<L, S>(P, x, y, g);
-                } else {
-                    gather_site_smem<S, R>(P, box, x0, y0, x, y, g);
-                }
-                if constexpr (EQ == EQ_ENERGY_MLP) {
-                    float a0[3];
-                    __syncwarp();
-                    mlp_site_start<T>(P, mslot.s, fluid, g, a0);
-                    if (fluid) pend = update_site<L, T, EQ>(P, g, x, y, t, nonfinite, nc, a0);
-                } else {
-                    if (fluid) pend = update_site<L, T, EQ>(P, g, x, y, t, nonfinite, nc);
-                }
-                if (inside) {
-#pragma unroll
-                    for (int i = 0; i < L::Q; i++) Store<S>::store(dst + i * plane + o, 0, g[i]);
-                }
-            }
-            warp_pend(P, sh.pend, &sh.npend, pend, (unsigned)(y * P.nx + x));
-        }
+        tma_tile<S, EQ, R>(P, box, tx * TX, ty * R, t, sh.pend, &sh.npend, mslot, nonfinite, nc);
         __syncthreads();
         // resolve the block's pending sites once its list could not take
         // another tile's, so that none overflow to the global list (which the

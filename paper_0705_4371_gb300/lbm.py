@@ -37,6 +37,12 @@ class lb_boundaries(C.Structure):
                 ("obstacle_h", C.c_int)]
 
 
+class lb_run_desc(C.Structure):
+    _fields_ = [("lattice", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("equilibrium", C.c_int),
+                ("nu", C.c_double), ("delta", C.c_double), ("k", C.c_int), ("bc", lb_boundaries),
+                ("precision", C.c_int)]
+
+
 _lib = None
 
 
@@ -77,6 +83,17 @@ def load(path=None):
         "lb_set_tile_shape": ([H, ip], ip),
         "lb_select_only_noalloc": ([vp, ip, dp, ip, vp, vp, vp], ip),
         "lb_mlp_init": ([vp, ip, C.c_ulonglong], ip),
+        "lb_batch_create": ([C.POINTER(lb_run_desc), ip, vp, C.POINTER(vp)], ip),
+        "lb_batch_destroy": ([vp], None),
+        "lb_batch_run": ([vp, ip], vp),
+        "lb_batch_step": ([vp, ip], ip),
+        "lb_batch_step_sequential": ([vp, ip], ip),
+        "lb_batch_sync": ([vp], ip),
+        "lb_batch_set_variant": ([vp, ip], ip),
+        "lb_batch_autotune": ([vp, ip, C.c_char_p, C.POINTER(ip)], ip),
+        "lb_batch_set_timing": ([vp, ip], ip),
+        "lb_batch_kernel_times": ([vp, C.POINTER(dp), C.POINTER(C.c_longlong), ip], ip),
+        "lb_batch_info": ([vp, vp], ip),
         "lb_energy_dataset": ([vp, vp, vp, vp, C.c_longlong, vp, vp, vp, vp, vp], ip),
         "lb_mlp_normalise": ([vp, vp, vp, C.c_longlong, vp], ip),
         "lb_mlp_forward": ([vp, vp, C.c_longlong, vp, vp], ip),
@@ -208,6 +225,17 @@ class Lattice:
         self.h = h
 
     @classmethod
+    def _borrow(cls, handle, lattice, nx, ny):
+        """A run owned by someone else (a batch): close() does not destroy it."""
+        self = cls.__new__(cls)
+        self.L = load()
+        self.lattice, self.nx, self.ny = lattice, nx, ny
+        self.q = 3 if lattice == LB_D1Q3 else 9
+        self.h = C.c_void_p(handle)
+        self._borrowed = True
+        return self
+
+    @classmethod
     def from_workload(cls, w, precision=LB_F32, stream=None, **over):
         """Create from a paper_0705_4371_gb300.inputs.Workload."""
         p = dict(nu=w.nu, delta=w.delta, k=w.k, equilibrium=w.eq)
@@ -218,7 +246,8 @@ class Lattice:
 
     def close(self):
         if getattr(self, "h", None):
-            self.L.lb_destroy(self.h)
+            if not getattr(self, "_borrowed", False):
+                self.L.lb_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -329,3 +358,83 @@ class Lattice:
                 "bytes_per_site": int(out[3]), "launches_per_step": int(out[4]),
                 "grid_blocks": int(out[5]), "blocks_per_sm": int(out[6]),
                 "tile_shape": int(out[7]), "beta": beta.value}
+
+
+class Batch:
+    """Many D2Q9 runs advanced together (lb_batch_*).  runs(r) gives run r as
+    a Lattice (owned by the batch) for initialisation and reading."""
+
+    def __init__(self, workloads, precision=LB_F32_DEV, stream=None, equilibrium=None):
+        self.L = load()
+        n = len(workloads)
+        descs = (lb_run_desc * n)()
+        for d, w in zip(descs, workloads):
+            d.lattice, d.nx, d.ny = LB_D2Q9, w.nx, w.ny
+            d.equilibrium = w.eq if equilibrium is None else equilibrium
+            d.nu, d.delta, d.k = w.nu, w.delta, w.k
+            d.bc = boundaries(w.bc, w.rho_in, w.u_in, w.obstacle)
+            d.precision = precision
+        h = C.c_void_p()
+        _check(self.L.lb_batch_create(descs, n, C.c_void_p(stream) if stream else None, C.byref(h)))
+        self.h = h
+        self.workloads = list(workloads)
+        self._runs = [Lattice._borrow(self.L.lb_batch_run(h, r), LB_D2Q9, w.nx, w.ny)
+                      for r, w in enumerate(workloads)]
+
+    def run(self, r):
+        return self._runs[r]
+
+    def __len__(self):
+        return len(self._runs)
+
+    def step(self, n=1):
+        _check(self.L.lb_batch_step(self.h, int(n)))
+
+    def step_sequential(self, n=1):
+        _check(self.L.lb_batch_step_sequential(self.h, int(n)))
+
+    def sync(self):
+        _check(self.L.lb_batch_sync(self.h))
+
+    def set_variant(self, v):
+        _check(self.L.lb_batch_set_variant(self.h, int(v)))
+
+    def autotune(self, steps=20, cache_path=None):
+        v = C.c_int(-1)
+        _check(self.L.lb_batch_autotune(self.h, int(steps), cache_path.encode() if cache_path else None,
+                                        C.byref(v)))
+        return v.value
+
+    def set_timing(self, enable):
+        _check(self.L.lb_batch_set_timing(self.h, int(enable)))
+
+    def kernel_times(self, reset=False):
+        ms, n = C.c_double(0), C.c_longlong(0)
+        _check(self.L.lb_batch_kernel_times(self.h, C.byref(ms), C.byref(n), int(reset)))
+        return {"ms": ms.value, "launches": n.value}
+
+    def info(self):
+        out = np.zeros(8, np.int64)
+        _check(self.L.lb_batch_info(self.h, _ptr(out)))
+        keys = ("runs", "sites", "tiles", "grid_blocks", "blocks_per_sm", "variant", "tile_rows",
+                "graph_steps")
+        return dict(zip(keys, (int(x) for x in out)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            for r in self._runs:
+                r.h = None
+            self.L.lb_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
