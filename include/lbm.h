@@ -320,11 +320,16 @@ const char* lb_last_error(void);
 
 /* ---- Batched form ------------------------------------------------------
  * Many independent D2Q9 runs (each one the method of Sec. 3.2 on its own
- * grid) advanced together: one kernel launch per time step covers the block
- * tiles of every run (a flat tile list taken by a persistent grid), and the
- * block that finishes a run's last tile performs that run's selection and
- * Ehrenfests' step.  Steps are replayed as CUDA graphs of 32.  Results are
- * bit-identical to stepping each run alone with lb_step.  The paper runs
+ * grid) advanced together and replayed as CUDA graphs of 32 steps, by one of
+ * three launch strategies (variants):
+ *   0, 1  the batched kernel: one launch per time step covers the block
+ *         tiles of every run (a flat tile list taken by a persistent grid;
+ *         8-row tiles with 2 stages, or 4-row tiles with 3 stages), and the
+ *         block that finishes a run's last tile performs that run's
+ *         selection and Ehrenfests' step;
+ *   2     every run's own stream-collide kernel, each run a chain of steps
+ *         in its own concurrent branch of the graph.
+ * Results are bit-identical to stepping each run alone with lb_step.  The paper runs
  * one flow at a time; the batch is this implementation's way to fill the
  * GPU with small runs (parameter sweeps). */
 typedef struct lb_run_desc {
@@ -360,8 +365,8 @@ int lb_batch_step_sequential(lb_batch* b, int n);
 
 int lb_batch_sync(lb_batch* b);
 
-/* Tile variant of the batched kernel: 0 = 8-row tiles, 2 stages; 1 =
- * 4-row tiles, 3 stages.  Synchronises. */
+/* Launch strategy (variant 0, 1 or 2, above; 0 after lb_batch_create).
+ * Synchronises. */
 int lb_batch_set_variant(lb_batch* b, int variant);
 
 /* Autotuner: when cache_path (may be NULL) holds an entry for this device

@@ -316,6 +316,12 @@ void run_advance(lb_handle* h, long long n) {
     if (n > 0) h->prestream = false;
 }
 
+int run_queue_step(lb_handle* h, int src, bool prestream, cudaStream_t st) {
+    const Params P = make_params(h, src, prestream);
+    CK(h->L.collide(P, h->tile_shape, &h->tmap[src], st));
+    return LB_OK;
+}
+
 int run_check(lb_handle* h) { return check_sticky(h, false); }
 
 int run_queue_err(lb_handle* h) { return queue_err_readback(h); }

@@ -1,7 +1,10 @@
-// lbm_batch.cu -- batched form: many independent D2Q9 runs advanced by one
-// kernel launch per time step (lbm_batch_kernels.cuh), replayed as CUDA
-// graphs, with a tile-variant autotuner whose choices are cached in a JSON
-// file.
+// lbm_batch.cu -- batched form: many independent D2Q9 runs advanced
+// together, replayed as CUDA graphs, with an autotuner over the launch
+// strategies whose choices are cached in a JSON file.  Strategies: the
+// batched kernel (one launch per step over the tiles of every run,
+// lbm_batch_kernels.cuh) with two tile shapes, or every run's own
+// stream-collide kernel in concurrent graph branches (one chain of steps per
+// run).  All compute identical results.
 #include <algorithm>
 #include <cctype>
 #include <cstdarg>
@@ -62,6 +65,10 @@ struct lb_batch {
     Params* h_params = nullptr;          // pinned staging of d_params
     std::vector<Params> uploaded;        // what d_params holds
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    // concurrent branches (variant 2): one stream per run, fork and join events
+    std::vector<cudaStream_t> rs;
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
     // timing of direct launches
     bool timing = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
@@ -84,7 +91,7 @@ void drop_graphs(lb_batch* b) {
 // Tile list, tensor maps and grid of the current variant.
 int configure(lb_batch* b) {
     drop_graphs(b);
-    b->BL = batch_launchers(b->storage, b->eq, b->variant);
+    b->BL = batch_launchers(b->storage, b->eq, std::min(b->variant, kBatchKernelVariants - 1));
     b->rows = b->BL.rows;
     int bps = 1;
     CK(b->BL.setup(&bps));
@@ -152,14 +159,50 @@ BatchArgs args_of(const lb_batch* b, int c) {
     return A;
 }
 
-int launch(lb_batch* b, int c, bool timed) {
+// Concurrent branches: every run advances `steps` steps on its own stream
+// (the first one reading a fresh state where it has one), between a fork
+// and a join on the batch stream.
+int branches(lb_batch* b, int c, int steps, bool first_pre) {
+    const int n = nruns(b);
+    if (b->rs.empty()) {
+        b->rs.assign(n, nullptr);
+        b->join.assign(n, nullptr);
+        for (int r = 0; r < n; r++) {
+            CK(cudaStreamCreateWithFlags(&b->rs[r], cudaStreamNonBlocking));
+            CK(cudaEventCreateWithFlags(&b->join[r], cudaEventDisableTiming));
+        }
+        CK(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+    }
+    CK(cudaEventRecord(b->fork, b->stream));
+    for (int r = 0; r < n; r++) {
+        lb_handle* h = b->runs[r];
+        CK(cudaStreamWaitEvent(b->rs[r], b->fork, 0));
+        const bool pre = first_pre && run_view(h).prestream;
+        int cc = c;
+        for (int s2 = 0; s2 < steps; s2++) {
+            const int rc = run_queue_step(h, cc, pre && s2 == 0, b->rs[r]);
+            if (rc != LB_OK) return rc;
+            cc = 1 - cc;
+        }
+        CK(cudaEventRecord(b->join[r], b->rs[r]));
+        CK(cudaStreamWaitEvent(b->stream, b->join[r], 0));
+    }
+    return LB_OK;
+}
+
+int launch(lb_batch* b, int c, bool timed, bool first_pre = false) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (timed) {
         CK(cudaEventCreate(&e0));
         CK(cudaEventCreate(&e1));
         CK(cudaEventRecord(e0, b->stream));
     }
-    CK(b->BL.launch(args_of(b, c), b->grid, b->stream));
+    if (b->variant >= kBatchKernelVariants) {
+        const int rc = branches(b, c, 1, first_pre);
+        if (rc != LB_OK) return rc;
+    } else {
+        CK(b->BL.launch(args_of(b, c), b->grid, b->stream));
+    }
     if (timed) {
         CK(cudaEventRecord(e1, b->stream));
         b->ev.push_back({e0, e1});
@@ -171,10 +214,14 @@ int build_graph(lb_batch* b, int start) {
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
     int rc = LB_OK;
-    int c = start;
-    for (int s = 0; s < kBatchGraphSteps && rc == LB_OK; s++) {
-        rc = launch(b, c, false);
-        c = 1 - c;
+    if (b->variant >= kBatchKernelVariants) {
+        rc = branches(b, start, kBatchGraphSteps, false);
+    } else {
+        int c = start;
+        for (int s = 0; s < kBatchGraphSteps && rc == LB_OK; s++) {
+            rc = launch(b, c, false);
+            c = 1 - c;
+        }
     }
     cudaError_t e = cudaStreamEndCapture(b->stream, &g);
     if (rc != LB_OK) {
@@ -340,6 +387,11 @@ void lb_batch_destroy(lb_batch* b) {
         cudaEventDestroy(p.first);
         cudaEventDestroy(p.second);
     }
+    for (cudaStream_t st : b->rs)
+        if (st) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : b->join)
+        if (ev) cudaEventDestroy(ev);
+    if (b->fork) cudaEventDestroy(b->fork);
     for (lb_handle* h : b->runs) lb_destroy(h);
     if (b->d_params) cudaFree(b->d_params);
     if (b->d_tmaps) cudaFree(b->d_tmaps);
@@ -373,7 +425,7 @@ int lb_batch_step(lb_batch* b, int n) {
     int done = 0;
     if (any_pre) {
         // first step after a state upload: the fresh runs read their own sites
-        rc = launch(b, c, b->timing);
+        rc = launch(b, c, b->timing, true);
         if (rc != LB_OK) return rc;
         c = 1 - c;
         done = 1;

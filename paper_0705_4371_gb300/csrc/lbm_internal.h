@@ -68,7 +68,11 @@ struct BatchLaunchers {
     int rows;                      // tile rows (the tile is 128 sites wide)
 };
 
-constexpr int kBatchVariants = 2;  // 0: 8-row tiles, 2 stages; 1: 4-row tiles, 3 stages
+// Launch strategies of a batch step: 0 and 1 = the batched kernel with
+// 8-row tiles and 2 stages, or 4-row tiles and 3 stages; 2 = every run's own
+// stream-collide kernel, in concurrent branches (one stream per run).
+constexpr int kBatchVariants = 3;
+constexpr int kBatchKernelVariants = 2;
 // storage: 0 = FP64, 1 = FP32, 2 = FP16; eq: EQ_POLY or EQ_ENTROPIC
 BatchLaunchers batch_launchers(int storage, int eq, int variant);
 BatchLaunchers batch_launchers_f64(int eq, int variant);
@@ -86,6 +90,8 @@ RunView run_view(const lb_handle* h);
 Params run_params(const lb_handle* h, int src, bool prestream);
 int run_tensor_map(const lb_handle* h, int buf, int rows, CUtensorMap* out);
 void run_advance(lb_handle* h, long long n);
+// One step of the run on stream st (its own kernel and tile shape).
+int run_queue_step(lb_handle* h, int src, bool prestream, cudaStream_t st);
 int run_check(lb_handle* h);
 int run_queue_err(lb_handle* h);
 int run_fail(int code, const char* msg);

@@ -1,7 +1,9 @@
-"""Batched form: many runs advanced by one launch per step.  Each run of a
-batch must evolve exactly as the same run stepped alone (same per-site
-arithmetic, same selection), for every storage type and tile variant, and
-replayed selections must reproduce the oracle's trajectories."""
+"""Batched form: many runs advanced together (the batched kernel, one launch
+per step over every run's tiles, or every run's own kernel in concurrent
+graph branches).  Each run of a batch must evolve exactly as the same run
+stepped alone (same per-site arithmetic, same selection), for every storage
+type and launch strategy, and replayed selections must reproduce the
+oracle's trajectories."""
 import ctypes as C
 import json
 
@@ -32,7 +34,8 @@ def mixed_runs():
             inputs.cylinder(520, 257, 12, 3000.0, delta=1e-5, k=8, name="b4")]
 
 
-@pytest.mark.parametrize("prec,variant", [("f32dev", 0), ("f32dev", 1), ("f16dev", 0), ("f64", 1), ("f32", 0)])
+@pytest.mark.parametrize("prec,variant", [("f32dev", 0), ("f32dev", 1), ("f32dev", 2), ("f16dev", 0),
+                                          ("f16dev", 2), ("f64", 1), ("f32", 0)])
 def test_batch_equals_runs_stepped_alone(lbm, prec, variant):
     ws = mixed_runs()
     P = lbm.PRECISIONS[prec]
@@ -119,15 +122,15 @@ def test_autotuner_times_variants_and_caches_the_choice(lbm, tmp_path):
         b.run(r).init_equilibrium(*inputs.cylinder_fields(w))
     cache = str(tmp_path / "autotune.json")
     v = b.autotune(steps=5, cache_path=cache)
-    assert v in (0, 1) and b.info()["variant"] == v
+    assert v in (0, 1, 2) and b.info()["variant"] == v
     d = json.load(open(cache))
     assert len(d) == 1
     (key, entry), = d.items()
-    assert entry["variant"] == v and len(entry["ms_per_step"]) == 2
+    assert entry["variant"] == v and len(entry["ms_per_step"]) == 3
     assert min(entry["ms_per_step"]) == entry["ms_per_step"][v]
     # a second batch of the same runs reads the cached choice
     b2 = lbm.Batch(ws, precision=lbm.LB_F32_DEV)
-    b2.set_variant(1 - v)
+    b2.set_variant((v + 1) % 3)
     assert b2.autotune(steps=5, cache_path=cache) == v
     assert len(json.load(open(cache))) == 1
     # the timing steps were real steps: runs stay consistent with each other
