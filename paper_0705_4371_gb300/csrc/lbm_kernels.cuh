@@ -166,14 +166,15 @@ __device__ __noinline__ double delta_s_fp64(PopArr<L::Q, T> g, double rho0) {
 // g: pre-collision deviations in, post-collision deviations out.
 // Returns true when the bound does not clear the site (dS may exceed delta):
 // its exact dS is then evaluated later from the unchanged source field.
-template <typename L, typename T, int EQ>
+// PROBE = false: the caller guarantees the site is not the probe site.
+template <typename L, typename T, int EQ, bool PROBE = true>
 __device__ __forceinline__ bool update_site(const Params& P, T* g, int x, int y, long long t,
                                             bool& nonfinite, NewtonCount& nc,
                                             const float* a0 = nullptr) {
     T gs[L::Q], rho, ux, uy;
     site_equilibrium<L, T, EQ>(P, g, gs, rho, ux, uy, nc, a0);
     nonfinite |= !isfinite(rho + ux + uy);
-    if (x == P.probe_x && y == P.probe_y && P.probe_ring)
+    if (PROBE && x == P.probe_x && y == P.probe_y && P.probe_ring)
         P.probe_ring[t % P.ring_cap] = (double)ux;
     T d[L::Q];
 #pragma unroll
@@ -821,14 +822,13 @@ __device__ __forceinline__ void gather_site_smem(const Params& P, const S* box, 
     }
 }
 
-// One staged tile: rows y0 .. y0 + R - 1 and columns x0 .. x0 + 127 of the
-// run P, from box (the tile's staged source planes); warp w computes row
-// y0 + w, lane l the sites x0 + l + 32 s.  Pending sites (dS not cleared by
-// the bound) are appended to the block's list.
+// The sites of a staged tile that touches a boundary, the obstacle or the
+// probe site, one by one with the boundary rules (kept out of line so that
+// the interior path is allocated registers on its own).
 template <typename S, int EQ, int R>
-__device__ __forceinline__ void tma_tile(const Params& P, const S* box, int x0, int y0, long long t,
-                                         unsigned* pend_list, unsigned* npend, MlpSlot<EQ>& mslot,
-                                         bool& nonfinite, NewtonCount& nc) {
+__device__ __noinline__ void tma_tile_general(const Params& P, const S* box, int x0, int y0, long long t,
+                                              unsigned* pend_list, unsigned* npend, MlpSlot<EQ>& mslot,
+                                              bool& nonfinite, NewtonCount& nc, bool clean) {
     using L = D2Q9;
     using T = typename Store<S>::T;
     using LY = TmaLayout<S, R>;
@@ -838,10 +838,6 @@ __device__ __forceinline__ void tma_tile(const Params& P, const S* box, int x0, 
     const int nxp = P.nxp, plane = (int)P.plane;
     const bool periodic = P.bc[0] == BC_PERIODIC || P.bc[2] == BC_PERIODIC;
     const int y = y0 + warp;
-    const bool clean = !P.prestream && x0 >= 1 && x0 + TX <= P.nx - 1 && y0 >= 1 &&
-                       y0 + R <= P.ny - 1 &&
-                       (P.ow == 0 || x0 + TX + 1 <= P.ox0 || x0 - 1 >= P.ox0 + P.ow ||
-                        y0 + R + 1 <= P.oy0 || y0 - 1 >= P.oy0 + P.oh);
     const S* sb = box + (warp + 1) * LY::W + LY::H;
 #pragma unroll 1
     for (int s = 0; s < TX / 32; s++) {
@@ -895,6 +891,59 @@ __device__ __forceinline__ void tma_tile(const Params& P, const S* box, int x0, 
     }
 }
 
+
+// One staged tile: rows y0 .. y0 + R - 1 and columns x0 .. x0 + 127 of the
+// run P, from box (the tile's staged source planes); warp w computes row
+// y0 + w, lane l the sites x0 + l + 32 s.  Pending sites (dS not cleared by
+// the bound) are appended to the block's list.
+template <typename S, int EQ, int R>
+__device__ __forceinline__ void tma_tile(const Params& P, const S* box, int x0, int y0, long long t,
+                                         unsigned* pend_list, unsigned* npend, MlpSlot<EQ>& mslot,
+                                         bool& nonfinite, NewtonCount& nc) {
+    using L = D2Q9;
+    using T = typename Store<S>::T;
+    using LY = TmaLayout<S, R>;
+    constexpr int TX = kTmaTX;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    S* __restrict__ dst = static_cast<S*>(P.dst);
+    const int nxp = P.nxp, plane = (int)P.plane;
+    const int y = y0 + warp;
+    const bool clean = !P.prestream && x0 >= 1 && x0 + TX <= P.nx - 1 && y0 >= 1 &&
+                       y0 + R <= P.ny - 1 &&
+                       (P.ow == 0 || x0 + TX + 1 <= P.ox0 || x0 - 1 >= P.ox0 + P.ow ||
+                        y0 + R + 1 <= P.oy0 || y0 - 1 >= P.oy0 + P.oh);
+    const S* sb = box + (warp + 1) * LY::W + LY::H;
+    // Interior tile without the probe site (almost every tile): every site is
+    // fluid and away from every boundary rule, so the sites take the shifted
+    // shared-memory reads with no per-site checks (the branch is uniform).
+    const bool probe_here = P.probe_ring && P.probe_y >= y0 && P.probe_y < y0 + R &&
+                            P.probe_x >= x0 && P.probe_x < x0 + TX;
+    if (clean && !probe_here) {
+        const int row = y * nxp + x0;
+        const unsigned site0 = (unsigned)(y * P.nx + x0);
+#pragma unroll 2
+        for (int s = 0; s < TX / 32; s++) {
+            const int c = lane + 32 * s;
+            T g[L::Q];
+#pragma unroll
+            for (int i = 0; i < L::Q; i++)
+                g[i] = Store<S>::load(sb + i * LY::PLANE + c - L::cx(i) - L::cy(i) * LY::W, 0);
+            bool pend;
+            if constexpr (EQ == EQ_ENERGY_MLP) {
+                float a0[3];
+                mlp_site_start<T>(P, mslot.s, true, g, a0);
+                pend = update_site<L, T, EQ, false>(P, g, x0 + c, y, t, nonfinite, nc, a0);
+            } else {
+                pend = update_site<L, T, EQ, false>(P, g, x0 + c, y, t, nonfinite, nc);
+            }
+#pragma unroll
+            for (int i = 0; i < L::Q; i++) Store<S>::store(dst + i * plane + row + c, 0, g[i]);
+            warp_pend(P, pend_list, npend, pend, site0 + (unsigned)c);
+        }
+        return;
+    }
+    tma_tile_general<S, EQ, R>(P, box, x0, y0, t, pend_list, npend, mslot, nonfinite, nc, clean);
+}
 template <typename S, int EQ, int R, int STAGES>
 __global__ void __launch_bounds__(32 * R, 16 / R)
     k_collide_d2q9_tma(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap tm) {
