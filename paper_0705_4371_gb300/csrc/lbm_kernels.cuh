@@ -944,8 +944,14 @@ __device__ __forceinline__ void tma_tile(const Params& P, const S* box, int x0, 
     }
     tma_tile_general<S, EQ, R>(P, box, x0, y0, t, pend_list, npend, mslot, nonfinite, nc, clean);
 }
+// Resident blocks per SM the staged kernel is compiled for: two (128
+// registers per thread) in general; three for FP16 storage, whose tiles take
+// half the shared memory (85 registers per thread).
+template <typename S, int R>
+constexpr int tma_min_blocks() { return sizeof(S) == 2 && R == 8 ? 3 : 16 / R; }
+
 template <typename S, int EQ, int R, int STAGES>
-__global__ void __launch_bounds__(32 * R, 16 / R)
+__global__ void __launch_bounds__(32 * R, tma_min_blocks<S, R>())
     k_collide_d2q9_tma(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap tm) {
     using L = D2Q9;
     using T = typename Store<S>::T;
