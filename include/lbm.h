@@ -300,11 +300,12 @@ int lb_kernel_times(lb_handle* h, double* collide_ms, long long* collide_launche
  * per thread in x, warps per block, minimum resident blocks per SM):
  * 0 = 1, 8, 3;  1 = 1, 8, 4;  2 = 2, 8, 2;  3 = 4, 8, 1.
  * Shared-memory-staged shapes (tensor-memory-accelerator copies of the
- * R x 128-site block tile of every population plane plus one halo row and
- * 16 bytes of halo columns; R rows, STAGES tiles in flight per block):
- * 4 = R 8, STAGES 2 (default);  5 = R 4, STAGES 3.
- * Results do not depend on the shape; only the speed does (the batched
- * runner's autotuner picks it per grid). */
+ * R x C-site block tile of every population plane plus one halo row and
+ * 16 bytes of halo columns; R rows, C columns, STAGES tiles in flight per
+ * block): 4 = 8 x 128, STAGES 2 (default);  5 = 4 x 128, STAGES 3;
+ * 6 = 8 x 64, STAGES 2 (three blocks per SM).  The energy-constrained forms
+ * are built for shapes 1 (their default) and 4 (shapes 5 and 6 run 4).
+ * Results do not depend on the shape; only the speed does. */
 int lb_set_tile_shape(lb_handle* h, int shape);
 
 /* Run facts (out: 8 entries): out[0] = Q, out[1] = padded row length

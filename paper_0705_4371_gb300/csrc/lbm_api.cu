@@ -234,7 +234,7 @@ bool valid_kind(int k) { return k >= LB_BB && k <= LB_PERIODIC; }
 // plane: Q) for staged tiles of R = rows rows: box = (128 + 2 H) x (R + 2)
 // x 1 elements, H = 16 bytes of halo on each side and one row above and
 // below; coordinates outside the array read as zero.
-int encode_tensor_map(const lb_handle* h, int b, int rows, CUtensorMap* out) {
+int encode_tensor_map(const lb_handle* h, int b, int rows, int cols, CUtensorMap* out) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
         void* fn = nullptr;
@@ -251,7 +251,7 @@ int encode_tensor_map(const lb_handle* h, int b, int rows, CUtensorMap* out) {
                                                            : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     const cuuint64_t gdim[3] = {(cuuint64_t)h->nx, (cuuint64_t)h->ny, (cuuint64_t)h->Q};
     const cuuint64_t gstride[2] = {(cuuint64_t)h->nxp * es, (cuuint64_t)h->plane * es};
-    const cuuint32_t box[3] = {(cuuint32_t)(128 + 2 * (16 / es)), (cuuint32_t)(rows + 2), 1};
+    const cuuint32_t box[3] = {(cuuint32_t)(cols + 2 * (16 / es)), (cuuint32_t)(rows + 2), 1};
     const cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = encode(out, dt, 3, h->buf[b], gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -264,7 +264,7 @@ int make_tensor_maps(lb_handle* h) {
     const int rows = staged_rows(h->tile_shape);
     if (h->lattice != LB_D2Q9 || rows == 0) return LB_OK;
     for (int b = 0; b < 2; b++) {
-        const int rc = encode_tensor_map(h, b, rows, &h->tmap[b]);
+        const int rc = encode_tensor_map(h, b, rows, staged_cols(h->tile_shape), &h->tmap[b]);
         if (rc != LB_OK) return rc;
     }
     return LB_OK;
@@ -307,7 +307,7 @@ RunView run_view(const lb_handle* h) {
 Params run_params(const lb_handle* h, int src, bool prestream) { return make_params(h, src, prestream); }
 
 int run_tensor_map(const lb_handle* h, int buf, int rows, CUtensorMap* out) {
-    return encode_tensor_map(h, buf, rows, out);
+    return encode_tensor_map(h, buf, rows, 128, out);
 }
 
 void run_advance(lb_handle* h, long long n) {

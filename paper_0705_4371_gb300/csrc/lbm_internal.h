@@ -32,10 +32,14 @@ Launchers launchers_f64_energy(int eq);
 Launchers launchers_f32_energy(int eq);
 Launchers launchers_f16_energy(int eq);
 
-constexpr int kTileShapes = 6;   // tile shapes of the D2Q9 stream-collide kernel
+constexpr int kTileShapes = 7;   // tile shapes of the D2Q9 stream-collide kernel
 
-// Rows per block tile of the shared-memory-staged shapes (0: not staged).
-inline int staged_rows(int tile_shape) { return tile_shape == 4 ? 8 : (tile_shape == 5 ? 4 : 0); }
+// Rows and columns per block tile of the shared-memory-staged shapes
+// (rows 0: not staged).
+inline int staged_rows(int tile_shape) {
+    return tile_shape == 4 || tile_shape == 6 ? 8 : (tile_shape == 5 ? 4 : 0);
+}
+inline int staged_cols(int tile_shape) { return tile_shape == 6 ? 64 : 128; }
 
 // message returned by lb_last_error on this thread
 void set_last_error(const char* msg);

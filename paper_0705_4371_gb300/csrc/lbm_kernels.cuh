@@ -735,10 +735,10 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, in
         : "memory");
 }
 
-template <typename S, int R>
+template <typename S, int R, int TX = kTmaTX>
 struct TmaLayout {
     static constexpr int H = 16 / (int)sizeof(S);          // halo columns (16 bytes)
-    static constexpr int W = kTmaTX + 2 * H;               // staged row length
+    static constexpr int W = TX + 2 * H;                   // staged row length
     static constexpr int ROWS = R + 2;                     // staged rows: y0 - 1 .. y0 + R
     static constexpr int BOX_BYTES = ROWS * W * (int)sizeof(S);
     static constexpr int PLANE_BYTES = (BOX_BYTES + 127) / 128 * 128;   // 128-byte aligned boxes
@@ -756,9 +756,9 @@ struct TmaShared {
     int tile[8];   // tile held by each stage (-1: none left)
 };
 
-template <typename S, int R, int STAGES, int EQ>
+template <typename S, int R, int STAGES, int EQ, int TX = kTmaTX>
 constexpr size_t tma_smem_bytes() {
-    return 128 + (size_t)STAGES * TmaLayout<S, R>::STAGE_BYTES + 8 * STAGES + sizeof(TmaShared) + 16 +
+    return 128 + (size_t)STAGES * TmaLayout<S, R, TX>::STAGE_BYTES + 8 * STAGES + sizeof(TmaShared) + 16 +
            (EQ == EQ_ENERGY_MLP ? sizeof(MlpSlot<EQ>) + 16 : 0);
 }
 
@@ -766,12 +766,12 @@ constexpr size_t tma_smem_bytes() {
 // memory: the same rules as gather_site (free flight, Sec. 4.2 boundaries),
 // reading box[i][row][col] with row = y - y0 + 1, col = x - x0 + H.  Not used
 // with periodic sides (their sources lie outside the box).
-template <typename S, int R>
+template <typename S, int R, int TX = kTmaTX>
 __device__ __forceinline__ void gather_site_smem(const Params& P, const S* box, int x0, int y0, int x,
                                                  int y, typename Store<S>::T* g) {
     using L = D2Q9;
     using T = typename Store<S>::T;
-    using LY = TmaLayout<S, R>;
+    using LY = TmaLayout<S, R, TX>;
     auto at = [&](int i, int sx, int sy) {
         return Store<S>::load(box + i * LY::PLANE + (sy - y0 + 1) * LY::W + (sx - x0 + LY::H), 0);
     };
@@ -825,14 +825,13 @@ __device__ __forceinline__ void gather_site_smem(const Params& P, const S* box, 
 // The sites of a staged tile that touches a boundary, the obstacle or the
 // probe site, one by one with the boundary rules (kept out of line so that
 // the interior path is allocated registers on its own).
-template <typename S, int EQ, int R>
+template <typename S, int EQ, int R, int TX>
 __device__ __noinline__ void tma_tile_general(const Params& P, const S* box, int x0, int y0, long long t,
                                               unsigned* pend_list, unsigned* npend, MlpSlot<EQ>& mslot,
                                               bool& nonfinite, NewtonCount& nc, bool clean) {
     using L = D2Q9;
     using T = typename Store<S>::T;
-    using LY = TmaLayout<S, R>;
-    constexpr int TX = kTmaTX;
+    using LY = TmaLayout<S, R, TX>;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     S* __restrict__ dst = static_cast<S*>(P.dst);
     const int nxp = P.nxp, plane = (int)P.plane;
@@ -872,7 +871,7 @@ __device__ __noinline__ void tma_tile_general(const Params& P, const S* box, int
             } else if (periodic) {
                 gather_site<L, S>(P, x, y, g);
             } else {
-                gather_site_smem<S, R>(P, box, x0, y0, x, y, g);
+                gather_site_smem<S, R, TX>(P, box, x0, y0, x, y, g);
             }
             if constexpr (EQ == EQ_ENERGY_MLP) {
                 float a0[3];
@@ -896,14 +895,13 @@ __device__ __noinline__ void tma_tile_general(const Params& P, const S* box, int
 // run P, from box (the tile's staged source planes); warp w computes row
 // y0 + w, lane l the sites x0 + l + 32 s.  Pending sites (dS not cleared by
 // the bound) are appended to the block's list.
-template <typename S, int EQ, int R>
+template <typename S, int EQ, int R, int TX = kTmaTX>
 __device__ __forceinline__ void tma_tile(const Params& P, const S* box, int x0, int y0, long long t,
                                          unsigned* pend_list, unsigned* npend, MlpSlot<EQ>& mslot,
                                          bool& nonfinite, NewtonCount& nc) {
     using L = D2Q9;
     using T = typename Store<S>::T;
-    using LY = TmaLayout<S, R>;
-    constexpr int TX = kTmaTX;
+    using LY = TmaLayout<S, R, TX>;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     S* __restrict__ dst = static_cast<S*>(P.dst);
     const int nxp = P.nxp, plane = (int)P.plane;
@@ -942,21 +940,23 @@ __device__ __forceinline__ void tma_tile(const Params& P, const S* box, int x0, 
         }
         return;
     }
-    tma_tile_general<S, EQ, R>(P, box, x0, y0, t, pend_list, npend, mslot, nonfinite, nc, clean);
+    tma_tile_general<S, EQ, R, TX>(P, box, x0, y0, t, pend_list, npend, mslot, nonfinite, nc, clean);
 }
 // Resident blocks per SM the staged kernel is compiled for: two (128
-// registers per thread) in general; three for FP16 storage, whose tiles take
-// half the shared memory (85 registers per thread).
-template <typename S, int R>
-constexpr int tma_min_blocks() { return sizeof(S) == 2 && R == 8 ? 3 : 16 / R; }
+// registers per thread) in general; three (85 registers per thread) where
+// the tiles take half the shared memory: FP16 storage, or FP32 tiles 64
+// sites wide.
+template <typename S, int R, int TX>
+constexpr int tma_min_blocks() {
+    return (sizeof(S) == 2 && R == 8) || (sizeof(S) == 4 && TX == 64 && R == 8) ? 3 : 16 / R;
+}
 
-template <typename S, int EQ, int R, int STAGES>
-__global__ void __launch_bounds__(32 * R, tma_min_blocks<S, R>())
+template <typename S, int EQ, int R, int STAGES, int TX = kTmaTX>
+__global__ void __launch_bounds__(32 * R, tma_min_blocks<S, R, TX>())
     k_collide_d2q9_tma(const __grid_constant__ Params P, const __grid_constant__ CUtensorMap tm) {
     using L = D2Q9;
     using T = typename Store<S>::T;
-    using LY = TmaLayout<S, R>;
-    constexpr int TX = kTmaTX;
+    using LY = TmaLayout<S, R, TX>;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
     S* stages = reinterpret_cast<S*>(smem);
@@ -1026,7 +1026,7 @@ __global__ void __launch_bounds__(32 * R, tma_min_blocks<S, R>())
         }
         const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
         const S* box = stages + (size_t)st * (LY::STAGE_BYTES / sizeof(S));
-        tma_tile<S, EQ, R>(P, box, tx * TX, ty * R, t, sh.pend, &sh.npend, mslot, nonfinite, nc);
+        tma_tile<S, EQ, R, TX>(P, box, tx * TX, ty * R, t, sh.pend, &sh.npend, mslot, nonfinite, nc);
         __syncthreads();
         // resolve the block's pending sites once its list could not take
         // another tile's, so that none overflow to the global list (which the
@@ -1211,6 +1211,8 @@ __global__ void k_export(const __grid_constant__ Params P, int mode, double* o0,
 // Launchers for one storage type.  Tile shapes of the D2Q9 kernel (sites per
 // thread in x, warps per block, minimum resident blocks per SM):
 //   0: 1, 8, 3     1: 1, 8, 4     2: 2, 8, 2     3: 4, 8, 1
+// and of the staged kernel (rows x columns per block tile, tiles in flight):
+//   4: 8 x 128, 2     5: 4 x 128, 3     6: 8 x 64, 2
 // The persistent grid is (resident blocks per SM) x (SM count), from the
 // occupancy calculator, capped by the number of row tiles.
 // ---------------------------------------------------------------------------
@@ -1230,24 +1232,24 @@ cudaError_t occupancy_d2q9(int* per_sm) {
                                                          32 * WARPS, 0);
 }
 
-template <typename S, int EQ, int R, int STAGES>
+template <typename S, int EQ, int R, int STAGES, int TX = kTmaTX>
 cudaError_t launch_d2q9_tma(const Params& P, const void* tmap, cudaStream_t st) {
-    constexpr size_t smem = tma_smem_bytes<S, R, STAGES, EQ>();
-    const long long tiles = (long long)((P.nx + kTmaTX - 1) / kTmaTX) * ((P.ny + R - 1) / R);
+    constexpr size_t smem = tma_smem_bytes<S, R, STAGES, EQ, TX>();
+    const long long tiles = (long long)((P.nx + TX - 1) / TX) * ((P.ny + R - 1) / R);
     const long long want = (tiles + 3) / 4;   // at least 4 tiles per block
     const unsigned blocks = (unsigned)std::max(1ll, std::min(want, (long long)P.grid_blocks));
-    k_collide_d2q9_tma<S, EQ, R, STAGES><<<blocks, 32 * R, smem, st>>>(
+    k_collide_d2q9_tma<S, EQ, R, STAGES, TX><<<blocks, 32 * R, smem, st>>>(
         P, *static_cast<const CUtensorMap*>(tmap));
     return cudaGetLastError();
 }
 
-template <typename S, int EQ, int R, int STAGES>
+template <typename S, int EQ, int R, int STAGES, int TX = kTmaTX>
 cudaError_t setup_d2q9_tma(int* per_sm) {
-    constexpr size_t smem = tma_smem_bytes<S, R, STAGES, EQ>();
-    cudaError_t e = cudaFuncSetAttribute(k_collide_d2q9_tma<S, EQ, R, STAGES>,
+    constexpr size_t smem = tma_smem_bytes<S, R, STAGES, EQ, TX>();
+    cudaError_t e = cudaFuncSetAttribute(k_collide_d2q9_tma<S, EQ, R, STAGES, TX>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_collide_d2q9_tma<S, EQ, R, STAGES>,
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_collide_d2q9_tma<S, EQ, R, STAGES, TX>,
                                                          32 * R, smem);
 }
 
@@ -1265,6 +1267,7 @@ struct LaunchImpl {
                 case 3: return launch_d2q9<S, EQ, 4, 8, 1>(P, st);
                 case 4: return launch_d2q9_tma<S, EQ, 8, 2>(P, tmap, st);
                 case 5: return launch_d2q9_tma<S, EQ, 4, 3>(P, tmap, st);
+                case 6: return launch_d2q9_tma<S, EQ, 8, 2, 64>(P, tmap, st);
                 default: return launch_d2q9<S, EQ, 1, 8, 3>(P, st);
             }
         } else {
@@ -1288,6 +1291,7 @@ struct LaunchImpl {
                 case 3: return occupancy_d2q9<S, EQ, 4, 8, 1>(per_sm);
                 case 4: return setup_d2q9_tma<S, EQ, 8, 2>(per_sm);
                 case 5: return setup_d2q9_tma<S, EQ, 4, 3>(per_sm);
+                case 6: return setup_d2q9_tma<S, EQ, 8, 2, 64>(per_sm);
                 default: return occupancy_d2q9<S, EQ, 1, 8, 3>(per_sm);
             }
         }

@@ -238,7 +238,7 @@ def test_beta_half_all_sites_equals_lbgk(lbm):
 
 
 @pytest.mark.parametrize("prec", ["f32", "f16dev", "f64"])
-@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4, 5, 6])
 def test_tile_shapes_give_identical_results(lbm, shape, prec):
     # 328 x 150: several 128-site tiles per row, ragged in x and y, obstacle
     # and all boundary kinds inside staged tiles
