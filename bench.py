@@ -286,8 +286,10 @@ def run_gpu(args):
 
     if args.forms and args.learned and rank == 0:
         forms["learned"] = learned_form(args, stream)
-    if args.forms and args.batched and rank == 0:
-        forms["batched"] = batched_form(args, stream, peaks)
+    if args.forms and args.batched:
+        bf = batched_form(args, stream, peaks, world, rank)   # every rank takes its share of the runs
+        if rank == 0:
+            forms["batched"] = bf
 
     cpu = cpu_baseline(w, args) if (rank == 0 and world == 1 and not args.no_cpu) else None
     clk = clocks.summary()
@@ -374,37 +376,55 @@ def learned_form(args, stream):
     return out
 
 
-def batched_form(args, stream, peaks):
+def batched_form(args, stream, peaks, world=1, rank=0):
     """64 cylinder runs (sizes 256 x 128 .. 2048 x 1024, Re, delta and k
     drawn per run, seeded) in FP32 deviation storage: aggregate MLUPS of
     every launch strategy of the batch (graphs of 32 steps), the
     autotuner's choice, and the same runs stepped one after another (each
-    through its own graphs)."""
+    through its own graphs).  Under torchrun the runs are split whole over
+    the ranks (sharding.assign_runs; no exchange), each timed region is
+    bracketed by barriers and reduced with a max over ranks."""
     import tempfile
     import torch
     from paper_0705_4371_gb300 import lbm
-    ws = inputs.workload_c5()
-    out = {"workload": "64 cylinder runs (c5 recipe, seed %d)" % inputs.SEED_CYLINDER, "storage": "f32dev"}
+    from paper_0705_4371_gb300.sharding import assign_runs, max_over_ranks
+    ws_all = inputs.workload_c5()
+    share = assign_runs([w.nx * w.ny for w in ws_all], world)[rank]
+    ws = [ws_all[i] for i in share]
+    total_sites = sum(w.nx * w.ny for w in ws_all)
+    out = {"workload": "64 cylinder runs (c5 recipe, seed %d)" % inputs.SEED_CYLINDER, "storage": "f32dev",
+           "ranks": world, "scaling": "strong" if world > 1 else None}
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    if not ws:
+        raise SystemExit("rank %d has no runs of the batch" % rank)
     with lbm.Batch(ws, precision=lbm.LB_F32_DEV, stream=stream.cuda_stream) as b:
         for r, w in enumerate(ws):
             b.run(r).init_equilibrium(*inputs.cylinder_fields(w))
         b.step(args.batch_spinup)
         b.sync()
-        cache = args.autotune_cache or os.path.join(tempfile.gettempdir(), "lbm_gb300_autotune.json")
+        cache = args.autotune_cache or os.path.join(tempfile.gettempdir(),
+                                                    "lbm_gb300_autotune_rank%d.json" % rank)
         t0 = time.perf_counter()
         v = b.autotune(steps=10, cache_path=cache)
         info = b.info()
-        out.update({"runs": info["runs"], "sites": info["sites"], "tiles": info["tiles"],
+        out.update({"runs": len(ws_all), "sites": total_sites, "runs_rank0": info["runs"],
                     "autotuned_variant": v, "autotune_s": round(time.perf_counter() - t0, 3)})
 
         def timed(fn, n):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
+            barrier()
             e0.record(stream)
             fn(n)
             e1.record(stream)
             torch.cuda.synchronize()
-            return e0.elapsed_time(e1)
+            barrier()
+            return max_over_ranks(e0.elapsed_time(e1), device="cuda")
 
         n = args.batch_steps
         names = {0: "batched_kernel_8row", 1: "batched_kernel_4row", 2: "concurrent_run_kernels"}
@@ -413,7 +433,7 @@ def batched_form(args, stream, peaks):
             b.set_variant(var)
             b.step(32)
             ms = timed(b.step, n)
-            variants[names[var]] = {"variant": var, "MLUPS": round(info["sites"] * n / (ms * 1e-3) / 1e6, 1),
+            variants[names[var]] = {"variant": var, "MLUPS": round(total_sites * n / (ms * 1e-3) / 1e6, 1),
                                     "ms_per_step": round(ms / n, 4),
                                     "launches_per_step": 1 if var < 2 else len(ws)}
         b.set_variant(v)
@@ -422,18 +442,18 @@ def batched_form(args, stream, peaks):
         ms_s = timed(b.step_sequential, n)
         b.sync()
         bytes_site = 72
-        ach = bytes_site * info["sites"] / (ms_b / n * 1e-3) / 1e9
+        ach = bytes_site * total_sites / (ms_b / n * 1e-3) / 1e9 / world
         out.update({
-            "chosen": {"variant": v, "MLUPS": round(info["sites"] * n / (ms_b * 1e-3) / 1e6, 1),
+            "chosen": {"variant": v, "MLUPS": round(total_sites * n / (ms_b * 1e-3) / 1e6, 1),
                        "ms_per_step": round(ms_b / n, 4)},
             "variants": variants,
-            "sequential": {"MLUPS": round(info["sites"] * n / (ms_s * 1e-3) / 1e6, 1),
+            "sequential": {"MLUPS": round(total_sites * n / (ms_s * 1e-3) / 1e6, 1),
                            "ms_per_step": round(ms_s / n, 4), "launches_per_step": len(ws)},
             "speedup_vs_sequential": round(ms_s / ms_b, 3), "steps": n,
             "roofline": {"bound": "hbm", "algorithmic_bytes_per_site": bytes_site,
                          "achieved_GBps": round(ach, 1), "peak": peaks["hbm_gbs"],
                          "frac": round(ach / peaks["hbm_gbs"], 4),
-                         "note": "whole step (concurrent kernels): algorithmic bytes / step time"}})
+                         "note": "whole step (concurrent kernels): algorithmic bytes / step time, per GPU"}})
     return out
 
 

@@ -79,3 +79,70 @@ def shock_tube(w, steps=None, precision=lbm.LB_F64, k=None, delta=None, nu=None)
     finally:
         g.close()
     return r[0], u[0], counts
+
+
+# --------------------------------------------------------------------------
+# Small cases for profiling (python -m paper_0705_4371_gb300.experiments ...)
+# --------------------------------------------------------------------------
+
+def energy_case(eq, steps=3, nx=512, ny=256):
+    """The energy-constrained cylinder (Re 5000, k 64) with the smooth energy
+    pattern, FP32 storage, `steps` directly launched steps; eq 3 first trains
+    a network on 2e6 samples.  Prints the kernel time and Newton iterations."""
+    w = inputs.cylinder(nx, ny, 16, 5000.0, k=64, eq=inputs.EQ_ENERGY)
+    rho, ux, uy = inputs.cylinder_fields(w, noise=1e-2)
+    with lbm.Lattice.from_workload(w, precision=lbm.LB_F64) as iso:
+        iso.init_equilibrium(rho, ux, uy)
+        e2 = iso.moments()[3] * inputs.energy_factor(w)
+    with lbm.Lattice.from_workload(w, precision=lbm.LB_F32, equilibrium=eq) as g:
+        if eq == lbm.LB_EQ_ENTROPIC_ENERGY_MLP:
+            from . import learned
+            p, _ = learned.train_energy_mlp(n=2_000_000, epochs=10, batch=4096, lr0=2e-3, lr1=2e-5)
+            g.set_mlp(p)
+        g.init_equilibrium(rho, ux, uy, e2)
+        g.set_timing(True)
+        g.step(steps)
+        g.sync()
+        kt = g.kernel_times()
+        s = g.newton_stats()
+        print("energy case eq %d: %.4f ms per launch, FP32 / FP64 Newton iterations per site %.3f / %.3f"
+              % (eq, kt["collide_ms"] / kt["collide_launches"], s[0] / s[2], s[1] / s[2]))
+
+
+def batch_case(nruns=24, steps=44, variant=0):
+    """The first nruns runs of the 64-run batch (FP32 deviation storage):
+    40 steps, then `steps - 40` directly launched (timed) steps."""
+    ws = inputs.workload_c5()[:nruns]
+    with lbm.Batch(ws, precision=lbm.LB_F32_DEV) as b:
+        b.set_variant(variant)
+        for r, w in enumerate(ws):
+            b.run(r).init_equilibrium(*inputs.cylinder_fields(w))
+        b.step(40)
+        b.set_timing(True)
+        b.step(max(1, steps - 40))
+        b.sync()
+        kt = b.kernel_times()
+        print("batch case: %d runs, %d sites, %.4f ms per step" % (nruns, b.info()["sites"], kt["ms"] / kt["launches"]))
+
+
+def main(argv=None):
+    import argparse
+    ap = argparse.ArgumentParser(description="small GPU cases of the learned and batched forms")
+    sub = ap.add_subparsers(dest="case", required=True)
+    e = sub.add_parser("energy")
+    e.add_argument("--eq", type=int, default=2)
+    e.add_argument("--steps", type=int, default=3)
+    b = sub.add_parser("batch")
+    b.add_argument("--runs", type=int, default=24)
+    b.add_argument("--steps", type=int, default=44)
+    b.add_argument("--variant", type=int, default=0)
+    a = ap.parse_args(argv)
+    lbm.load()
+    if a.case == "energy":
+        energy_case(a.eq, a.steps)
+    else:
+        batch_case(a.runs, a.steps, a.variant)
+
+
+if __name__ == "__main__":
+    main()
