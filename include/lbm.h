@@ -79,12 +79,20 @@ enum lb_precision { LB_F64 = 0, LB_F32 = 1, LB_F32_DEV = 2, LB_F16_DEV = 3 };
  *   LB_INLET_EQ   incoming populations = quasiequilibrium of (rho_in, u_in)
  *                 (x sides only);
  *   LB_OUTLET_EQ  incoming populations = quasiequilibrium of the density and
- *                 velocity of the penultimate column (x sides only);
- *   LB_PERIODIC   wrap-around (both sides of an axis).
+ *                 velocity of the penultimate column (x sides only; the
+ *                 outlet rule of Sec. 4.2);
+ *   LB_PERIODIC   wrap-around (both sides of an axis);
+ *   LB_OUTLET_COPY zero-gradient outflow: an incoming population arrives as
+ *                 if the column beyond the side were a copy of the side
+ *                 column (it is taken from the side column itself, row
+ *                 y - v_y, or y where that leaves the lattice; x sides only).
+ *                 Not in the paper: its equilibrium outlet feeds back the
+ *                 reverse flow of vortices leaving the channel.
  * The obstacle is a solid rectangle [x0, x0+w) x [y0, y0+h) (w = 0: none)
  * with half-way bounce-back on its faces; it must keep at least one fluid
  * site to the y walls and two columns to an outlet. */
-enum lb_bc { LB_BB = 0, LB_FREESLIP = 1, LB_INLET_EQ = 2, LB_OUTLET_EQ = 3, LB_PERIODIC = 4 };
+enum lb_bc { LB_BB = 0, LB_FREESLIP = 1, LB_INLET_EQ = 2, LB_OUTLET_EQ = 3, LB_PERIODIC = 4,
+             LB_OUTLET_COPY = 5 };
 
 typedef struct lb_boundaries {
     int kind_x0, kind_x1, kind_y0, kind_y1;

@@ -41,7 +41,7 @@
 enum { ORA_D1Q3 = 0, ORA_D2Q9 = 1 };
 enum { ORA_EQ_POLY = 0, ORA_EQ_ENTROPIC = 1, ORA_EQ_ENERGY = 2 };
 enum { ORA_BC_BB = 0, ORA_BC_FREESLIP = 1, ORA_BC_INLET = 2,
-       ORA_BC_OUTLET = 3, ORA_BC_PERIODIC = 4 };
+       ORA_BC_OUTLET = 3, ORA_BC_PERIODIC = 4, ORA_BC_OUTLET_COPY = 5 };
 
 /* D1Q3, paper numbering {v1, v2, v3} = {0, -1, +1} (Sec. 4.1): static,
  * left-moving, right-moving.  The weights are not printed; they are read
@@ -459,6 +459,10 @@ static long site(const ora_cfg* c, int x, int y) { return (long)y * c->nx + x; }
  *  - x side OUTLET: incoming populations take the quasiequilibrium of the
  *                   density and velocity of the penultimate column (x = nx-2,
  *                   same row) of the post-collision field;
+ *  - x side OUTLET_COPY (zero-gradient outflow; the paper's outlet is the
+ *                   one above): the column beyond the side is read as a copy
+ *                   of the side column (source column x instead of x - v_x),
+ *                   then the y and obstacle rules apply as usual;
  *  - BB           : half-way bounce-back, f_i(x) = fp_{-i}(x);
  *  - PERIODIC     : wrap around;
  *  - y side FREESLIP: specular reflection, the population (v_x, -v_y) that
@@ -490,6 +494,8 @@ static void gather_site(const ora_cfg* c, const double* fp, int x, int y, double
                 feq_rho_u(L, c->eq, M[0], M[1] / M[0], L == ORA_D1Q3 ? 0.0 : M[2] / M[0], fs);
                 f[i] = fs[i];
                 continue;
+            } else if (kind == ORA_BC_OUTLET_COPY) {
+                sx = x;
             } else { /* BB (FREESLIP is not accepted on x sides) */
                 int o = lat_find(L, -cx, -cy);
                 f[i] = fp[o * N + s0];

@@ -228,7 +228,7 @@ int build_graph(lb_handle* h, int start) {
     return LB_OK;
 }
 
-bool valid_kind(int k) { return k >= LB_BB && k <= LB_PERIODIC; }
+bool valid_kind(int k) { return k >= LB_BB && k <= LB_OUTLET_COPY; }
 
 // Tensor map describing population buffer b as a 3-D array (x: nx, y: ny,
 // plane: Q) for staged tiles of R = rows rows: box = (128 + 2 H) x (R + 2)
@@ -381,7 +381,7 @@ int lb_create(int lattice, int nx, int ny, int equilibrium, double nu, double de
     if (b.kind_x0 == LB_FREESLIP || b.kind_x1 == LB_FREESLIP)
         return fail(LB_ERR_ARG, "free-slip is supported on the y sides only");
     if (b.kind_y0 == LB_INLET_EQ || b.kind_y0 == LB_OUTLET_EQ || b.kind_y1 == LB_INLET_EQ ||
-        b.kind_y1 == LB_OUTLET_EQ)
+        b.kind_y1 == LB_OUTLET_EQ || b.kind_y0 == LB_OUTLET_COPY || b.kind_y1 == LB_OUTLET_COPY)
         return fail(LB_ERR_ARG, "inlet/outlet are supported on the x sides only");
     if ((b.kind_x0 == LB_PERIODIC) != (b.kind_x1 == LB_PERIODIC) ||
         (b.kind_y0 == LB_PERIODIC) != (b.kind_y1 == LB_PERIODIC))

@@ -60,7 +60,7 @@ static_assert(D2Q9::opp(5) == 7 && D2Q9::opp(6) == 8 && D2Q9::opp(7) == 5 && D2Q
 // Run parameters (passed by value to every kernel).
 // ---------------------------------------------------------------------------
 enum : int { EQ_POLY = 0, EQ_ENTROPIC = 1, EQ_ENERGY = 2, EQ_ENERGY_MLP = 3 };
-enum : int { BC_BB = 0, BC_FREESLIP = 1, BC_INLET = 2, BC_OUTLET = 3, BC_PERIODIC = 4 };
+enum : int { BC_BB = 0, BC_FREESLIP = 1, BC_INLET = 2, BC_OUTLET = 3, BC_PERIODIC = 4, BC_OUTLET_COPY = 5 };
 enum : unsigned { ERR_NONFINITE = 1u, ERR_NEWTON = 2u, ERR_TIMEOUT = 4u, ERR_REPLAY = 8u };
 
 struct Params {
@@ -410,6 +410,10 @@ __device__ void gather_site(const Params& P, int x, int y, typename Store<S>::T*
                 }
                 g[i] = gout[i];
                 continue;
+            } else if (kind == BC_OUTLET_COPY) {
+                // zero-gradient outflow: the column beyond the side is a copy
+                // of the side column; the y and obstacle rules then apply
+                sx = x;
             } else {
                 g[i] = Store<S>::load(P.src, L::opp(i) * P.plane + s0);
                 continue;

@@ -786,10 +786,13 @@ __device__ __forceinline__ void gather_site_smem(const Params& P, const S* box, 
 #pragma unroll
     for (int i = 0; i < L::Q; i++) {
         const int cx = L::cx(i), cy = L::cy(i);
-        const int sx = x - cx, sy = y - cy;
+        int sx = x - cx;
+        const int sy = y - cy;
         if (sx < 0 || sx >= P.nx) {
             const int kind = sx < 0 ? P.bc[0] : P.bc[1];
-            if (kind == BC_INLET) {
+            if (kind == BC_OUTLET_COPY) {
+                sx = x;   // the column beyond the side is a copy of the side column
+            } else if (kind == BC_INLET) {
                 if (!have_in) {
                     feq_rho_u<L, T>(P.eq, (T)P.rho_in, (T)P.ux_in, (T)P.uy_in, rho0, gin);
                     have_in = true;
@@ -811,7 +814,7 @@ __device__ __forceinline__ void gather_site_smem(const Params& P, const S* box, 
             } else {
                 g[i] = at(L::opp(i), x, y);
             }
-            continue;
+            if (kind != BC_OUTLET_COPY) continue;
         }
         if (sy < 0 || sy >= P.ny) {
             const int kind = sy < 0 ? P.bc[2] : P.bc[3];

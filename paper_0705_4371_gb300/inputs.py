@@ -45,7 +45,7 @@ class SplitMix64:
 # --------------------------------------------------------------------------
 # Boundary kinds (same numbering on both sides of the parity tests).
 # --------------------------------------------------------------------------
-BC_BB, BC_FREESLIP, BC_INLET, BC_OUTLET, BC_PERIODIC = 0, 1, 2, 3, 4
+BC_BB, BC_FREESLIP, BC_INLET, BC_OUTLET, BC_PERIODIC, BC_OUTLET_COPY = 0, 1, 2, 3, 4, 5
 D1Q3, D2Q9 = 0, 1
 EQ_POLY, EQ_ENTROPIC, EQ_ENERGY, EQ_ENERGY_MLP = 0, 1, 2, 3
 SEED_ENERGY_SAMPLES = 20070531
@@ -97,7 +97,7 @@ def shock_tube_fields(w: Workload):
 
 
 def cylinder(nx=600, ny=500, L=20, re=1000.0, u_inf=0.05, delta=1e-3, k=16,
-             steps=200000, eq=EQ_POLY, face_x=None, name=None, seed=SEED_CYLINDER):
+             steps=200000, eq=EQ_POLY, face_x=None, name=None, seed=SEED_CYLINDER, outlet=BC_OUTLET):
     """Square cylinder of side L in a free-slip channel (Sec. 4.2).
 
     Upstream face at x = 5L (face_x), centred in y; inlet at x = 0,
@@ -111,7 +111,7 @@ def cylinder(nx=600, ny=500, L=20, re=1000.0, u_inf=0.05, delta=1e-3, k=16,
     probe = (min(cxc + 4 * L, nx - 3), max(cyc - 2 * L, 1))
     nu = L * u_inf / re
     return Workload(name or "d2q9_cylinder_%dx%d_L%d_Re%g" % (nx, ny, L, re), D2Q9, nx, ny, eq,
-                    nu, delta, k, steps, (BC_INLET, BC_OUTLET, BC_FREESLIP, BC_FREESLIP),
+                    nu, delta, k, steps, (BC_INLET, outlet, BC_FREESLIP, BC_FREESLIP),
                     1.0, (u_inf, 0.0), (fx, oy0, L, L), probe, L, seed)
 
 
@@ -150,7 +150,9 @@ def workload_c1():
 
 
 def workload_c2(re=1000.0):
-    return cylinder(600, 500, 20, re)
+    """600 x 500 channel, L = 20 at 5L from the inlet, zero-gradient outflow."""
+    return cylinder(600, 500, 20, re, outlet=BC_OUTLET_COPY,
+                    name="d2q9_cylinder_600x500_L20_Re%g_zero_gradient_outlet" % re)
 
 
 def workload_c3():

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "liblbm.so")
 LB_D1Q3, LB_D2Q9 = 0, 1
 LB_EQ_POLY, LB_EQ_ENTROPIC, LB_EQ_ENTROPIC_ENERGY, LB_EQ_ENTROPIC_ENERGY_MLP = 0, 1, 2, 3
 LB_F64, LB_F32, LB_F32_DEV, LB_F16_DEV = 0, 1, 2, 3
-LB_BB, LB_FREESLIP, LB_INLET_EQ, LB_OUTLET_EQ, LB_PERIODIC = 0, 1, 2, 3, 4
+LB_BB, LB_FREESLIP, LB_INLET_EQ, LB_OUTLET_EQ, LB_PERIODIC, LB_OUTLET_COPY = 0, 1, 2, 3, 4, 5
 LB_OK, LB_ERR_ARG, LB_ERR_CUDA, LB_ERR_NONFINITE, LB_ERR_NEWTON, LB_ERR_TIMEOUT, LB_ERR_OOM, \
     LB_ERR_STATE = 0, -1, -2, -3, -4, -5, -6, -7
 

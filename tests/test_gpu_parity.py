@@ -37,6 +37,7 @@ def gpu_run(lbm, w, prec, **over):
 WORKLOADS = {
     "cyl_poly": lambda: small_cylinder(),
     "cyl_entropic": lambda: small_cylinder(eq=inputs.EQ_ENTROPIC),
+    "cyl_copy_outlet": lambda: inputs.cylinder(200, 72, 8, 20000.0, k=16, outlet=inputs.BC_OUTLET_COPY),
     "closed_box": lambda: inputs.Workload("box", inputs.D2Q9, 131, 37, inputs.EQ_POLY, 1e-3, 1e-4,
                                           8, 10, (inputs.BC_BB,) * 4, obstacle=(40, 10, 9, 7)),
     "periodic": lambda: inputs.Workload("per", inputs.D2Q9, 160, 40, inputs.EQ_ENTROPIC, 2e-3,
@@ -237,12 +238,14 @@ def test_beta_half_all_sites_equals_lbgk(lbm):
     assert b.counts(1)[0] == w.n_sites - w.L * w.L
 
 
+@pytest.mark.parametrize("outlet", ["eq", "copy"])
 @pytest.mark.parametrize("prec", ["f32", "f16dev", "f64"])
 @pytest.mark.parametrize("shape", [0, 1, 2, 3, 4, 5, 6])
-def test_tile_shapes_give_identical_results(lbm, shape, prec):
+def test_tile_shapes_give_identical_results(lbm, shape, prec, outlet):
     # 328 x 150: several 128-site tiles per row, ragged in x and y, obstacle
     # and all boundary kinds inside staged tiles
-    w = small_cylinder(re=20000.0, delta=1e-6, k=16, nx=328, ny=150, L=12)
+    w = inputs.cylinder(328, 150, 12, 20000.0, delta=1e-6, k=16,
+                        outlet=inputs.BC_OUTLET if outlet == "eq" else inputs.BC_OUTLET_COPY)
     rho, ux, uy = initial_fields(w, noise=1e-3)
     ref = gpu_run(lbm, w, prec)
     ref.set_tile_shape(1)
