@@ -23,7 +23,7 @@ class _Cfg(C.Structure):
                 ("eq", C.c_int), ("beta", C.c_double), ("delta", C.c_double),
                 ("k", C.c_long), ("bc", C.c_int * 4), ("rho_in", C.c_double),
                 ("ux_in", C.c_double), ("uy_in", C.c_double), ("ox0", C.c_int),
-                ("oy0", C.c_int), ("ow", C.c_int), ("oh", C.c_int)]
+                ("oy0", C.c_int), ("ow", C.c_int), ("oh", C.c_int), ("elbm", C.c_int)]
 
 
 def lib():
@@ -46,6 +46,8 @@ def lib():
         L.ora_perfect_entropy.argtypes = [C.c_int, dp]
         L.ora_perfect_entropy.restype = C.c_double
         L.ora_delta_s.argtypes = [C.c_int, dp, dp]
+        L.ora_elbm_alpha.argtypes = [C.c_int, dp, dp]
+        L.ora_elbm_alpha.restype = C.c_double
         L.ora_delta_s.restype = C.c_double
         L.ora_select.argtypes = [dp, C.c_void_p, C.c_long, C.c_double, C.c_long, lp]
         L.ora_select.restype = C.c_long
@@ -97,6 +99,7 @@ class Config:
     rho_in: float = 1.0
     u_in: tuple = (0.0, 0.0)
     obstacle: tuple = (0, 0, 0, 0)
+    elbm: bool = False        # collision (elbmLB) instead of (lbgkLB)
 
     @property
     def q(self):
@@ -114,6 +117,7 @@ class Config:
             s.bc[i] = self.bc[i]
         s.rho_in, s.ux_in, s.uy_in = self.rho_in, self.u_in[0], self.u_in[1]
         s.ox0, s.oy0, s.ow, s.oh = self.obstacle
+        s.elbm = 1 if self.elbm else 0
         return s
 
     def solid_mask(self):
@@ -174,6 +178,12 @@ def newton(lattice, Mn, mu0=None, tol=1e-12, maxit=100):
     mu = mu_guess(lattice, Mn) if mu0 is None else np.array(mu0, np.float64)
     it = lib().ora_newton(lattice, Mn, mu, tol, maxit)
     return mu, it
+
+
+def elbm_alpha(lattice, f, fs):
+    """ELBM parameter alpha of (elbmLB): S(f + alpha (f* - f)) = S(f)."""
+    return lib().ora_elbm_alpha(lattice, np.ascontiguousarray(f, np.float64),
+                                np.ascontiguousarray(fs, np.float64))
 
 
 def perfect_entropy(lattice, f):

@@ -392,6 +392,67 @@ double ora_delta_s(int lattice, const double* f, const double* fs)
 /* The paper is silent on ties: the total order (dS descending, site   */
 /* index ascending) is used.  Output indices are sorted ascending.     */
 /* ------------------------------------------------------------------ */
+/* ELBM (elbmLB): the parameter alpha of f + alpha beta (f* - f) solves the
+ * constant-entropy condition S(f + alpha (f* - f)) = S(f) (nontrivial root).
+ * With D = f* - f, x_i = alpha D_i / f_i and phi(x) = (1+x) ln(1+x) - x, and
+ * sum D = 0 (f* has the moments of f), the condition reads
+ *     sum f_i phi(alpha D_i / f_i) = alpha sum D_i ln(1 + D_i / f_i)
+ * (the left side minus the right side is -(S(f + alpha D) - S(f)), with
+ * no cancellation between two entropies).  Its left side over alpha is
+ * increasing (phi is convex, phi(0) = 0), so the root above alpha = 1 is
+ * unique.  Bisection (the paper's method) on [1, alpha_max] to 1e-15, with
+ * alpha_max the largest alpha keeping f + alpha D >= 0; when the entropy
+ * still exceeds S(f) at alpha_max, alpha = alpha_max.  f = f* (D = 0) gives
+ * the LBGK value alpha = 2.  Returns alpha; -1 for f outside the positive
+ * cone (f_i <= 0). */
+/* phi(x) = (1 + x) ln(1 + x) - x for x >= -1 (phi(-1) = 1); for |x| < 0.05
+ * its Taylor series sum_{n>=2} (-1)^n x^n / (n (n-1)) to n = 16 (the
+ * direct form loses the leading x^2 / 2 to cancellation there). */
+static double phi(double x)
+{
+    if (x <= -1.0) return 1.0;
+    if (fabs(x) < 0.05) {
+        double s = 0.0, p = x * x;
+        for (int n = 2; n <= 16; n++) {
+            s += ((n & 1) ? -1.0 : 1.0) * p / (double)(n * (n - 1));
+            p *= x;
+        }
+        return s;
+    }
+    return (1.0 + x) * log1p(x) - x;
+}
+
+static double elbm_gap(int q, const double* f, const double* D, double R, double alpha)
+{
+    double s = 0.0;
+    for (int i = 0; i < q; i++) s += f[i] * phi(alpha * D[i] / f[i]);
+    return s - alpha * R;
+}
+
+double ora_elbm_alpha(int lattice, const double* f, const double* fs)
+{
+    int q = ora_q(lattice);
+    double D[9], R = 0.0, amax = INFINITY;
+    int moved = 0;
+    for (int i = 0; i < q; i++) {
+        if (!(f[i] > 0.0) || !(fs[i] > 0.0)) return -1.0;
+        D[i] = fs[i] - f[i];
+        if (D[i] != 0.0) moved = 1;
+        if (D[i] < 0.0) amax = fmin(amax, f[i] / -D[i]);
+        R += D[i] * log1p(D[i] / f[i]);
+    }
+    if (!moved || !(R > 0.0)) return 2.0;
+    double lo = 1.0, hi = amax;
+    if (!isfinite(hi)) return 2.0;
+    if (elbm_gap(q, f, D, R, hi) <= 0.0) return hi;    /* no root before the positivity limit */
+    while (hi - lo > 1e-15 * hi) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (elbm_gap(q, f, D, R, mid) <= 0.0) lo = mid; else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
 typedef struct { double ds; long idx; } cand_t;
 
 static int cand_cmp(const void* pa, const void* pb)
@@ -440,6 +501,7 @@ typedef struct {
     int bc[4];       /* x = 0, x = nx-1, y = 0, y = ny-1 */
     double rho_in, ux_in, uy_in;   /* inlet state */
     int ox0, oy0, ow, oh;          /* solid rectangle; ow == 0: none */
+    int elbm;                      /* collision (elbmLB) instead of (lbgkLB) */
 } ora_cfg;
 
 static int is_solid(const ora_cfg* c, int x, int y)
@@ -656,14 +718,22 @@ int ora_run(const ora_cfg* c, double* f, long nsteps,
             for (long j = 0; j < m; j++) sel_log[sel_used + j] = sel[j];
             sel_used += m;
         }
-        /* 3. collision: Ehrenfests' step at chosen sites, LBGK elsewhere */
+        /* 3. collision: Ehrenfests' step at chosen sites, LBGK (or ELBM)
+         *    elsewhere */
 #pragma omp parallel for schedule(static)
         for (long s = 0; s < N; s++) {
+            double a = 2.0;
+            if (c->elbm && elig[s] && !chosen[s]) {
+                double gl[9], gs[9];
+                for (int i = 0; i < q; i++) { gl[i] = f[i * N + s]; gs[i] = fs[i * N + s]; }
+                a = ora_elbm_alpha(L, gl, gs);
+                if (a < 0.0) a = 2.0;   /* outside the positive cone: dS = +inf, LBGK */
+            }
             for (int i = 0; i < q; i++) {
                 double fi = f[i * N + s], fsi = fs[i * N + s];
                 if (!elig[s]) fp[i * N + s] = 0.0;
                 else if (chosen[s]) fp[i * N + s] = fsi;
-                else fp[i * N + s] = fi + 2.0 * c->beta * (fsi - fi);
+                else fp[i * N + s] = fi + a * c->beta * (fsi - fi);
             }
         }
         /* 4. free flight with boundary rules */
@@ -705,7 +775,16 @@ int ora_collide(const ora_cfg* c, const double* f, const long* sel, long m, doub
             double fi = f[i * N + s], fsi = fs[i * N + s];
             if (solid) fp[i * N + s] = 0.0;
             else if (chosen[s]) fp[i * N + s] = fsi;
-            else fp[i * N + s] = fi + 2.0 * c->beta * (fsi - fi);
+            else {
+                double a = 2.0;
+                if (c->elbm) {
+                    double gl[9], gs[9];
+                    for (int j = 0; j < q; j++) { gl[j] = f[j * N + s]; gs[j] = fs[j * N + s]; }
+                    a = ora_elbm_alpha(L, gl, gs);
+                    if (a < 0.0) a = 2.0;
+                }
+                fp[i * N + s] = fi + a * c->beta * (fsi - fi);
+            }
         }
     }
     free(fs); free(chosen);
