@@ -216,6 +216,16 @@ int lb_select_only_noalloc(const double* ds, int n, double delta, int k, int* id
  * for step t, their indices concatenated in idx.  Host arrays. */
 int lb_replay_selection(lb_handle* h, const int* counts, const int* idx, int nsteps);
 
+/* Collision (Sec. 4.1): LB_COLLISION_LBGK (lbgkLB, the default),
+ * f' = f + 2 beta (f* - f); or LB_COLLISION_ELBM (elbmLB),
+ * f' = f + alpha beta (f* - f) with alpha the nontrivial root of
+ * S(f + alpha (f* - f)) = S(f) per site (FP64, to 1e-15; alpha = 2 at
+ * f = f*; the positivity limit when the entropy still exceeds S(f) there).
+ * ELBM needs LB_EQ_ENTROPIC (LB_ERR_ARG otherwise); Ehrenfests' steps apply
+ * to it as to LBGK.  Synchronises the run's stream. */
+enum lb_collision { LB_COLLISION_LBGK = 0, LB_COLLISION_ELBM = 1 };
+int lb_set_collision(lb_handle* h, int collision);
+
 /* ---- Learned form ------------------------------------------------------
  * The 4-64-64-4 ReLU network that gives the energy Newton solve of
  * LB_EQ_ENTROPIC_ENERGY_MLP its start point.  The Lagrange form of the

@@ -104,6 +104,7 @@ struct lb_handle {
     // energy form; the learned form's network (FP32 master copy on the device)
     float* mlp;
     bool mlp_set;
+    bool elbm;                // ELBM collision (elbmLB)
     unsigned long long* newton_stats;
     // completion ticket of the stream-collide blocks; tile shape of K1
     unsigned* ticket;
@@ -150,6 +151,7 @@ Params make_params(const lb_handle* h, int src, bool prestream) {
     P.pend_count = h->pend_count;
     P.grid_blocks = h->grid_blocks;
     P.tile_counter = h->tile_counter;
+    P.elbm = h->elbm ? 1 : 0;
     return P;
 }
 
@@ -762,6 +764,18 @@ int lb_select_only(const double* ds, int n, double delta, int k, int* idx_out, i
     if (e != cudaSuccess)
         return fail(e == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA, "lb_select_only: %s",
                     cudaGetErrorString(e));
+    return LB_OK;
+}
+
+int lb_set_collision(lb_handle* h, int collision) {
+    if (!h) return fail(LB_ERR_ARG, "NULL handle");
+    if (collision != LB_COLLISION_LBGK && collision != LB_COLLISION_ELBM)
+        return fail(LB_ERR_ARG, "unknown collision %d", collision);
+    if (collision == LB_COLLISION_ELBM && h->eq != LB_EQ_ENTROPIC)
+        return fail(LB_ERR_ARG, "ELBM uses the entropic quasiequilibria (LB_EQ_ENTROPIC)");
+    CK(cudaStreamSynchronize(h->stream));
+    h->elbm = collision == LB_COLLISION_ELBM;
+    drop_graphs(h);
     return LB_OK;
 }
 

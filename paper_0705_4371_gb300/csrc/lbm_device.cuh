@@ -108,6 +108,7 @@ struct Params {
     unsigned* pend_count;
     int grid_blocks;          // persistent grid size (resident blocks x SMs)
     unsigned* tile_counter;   // next tile to hand out (staged shapes)
+    int elbm;                 // ELBM collision (elbmLB) instead of LBGK (entropic f* only)
 };
 
 template <int Q, typename T> struct PopArr { T v[Q]; };

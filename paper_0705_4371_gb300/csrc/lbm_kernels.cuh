@@ -166,6 +166,80 @@ __device__ __noinline__ double delta_s_fp64(PopArr<L::Q, T> g, double rho0) {
 // g: pre-collision deviations in, post-collision deviations out.
 // Returns true when the bound does not clear the site (dS may exceed delta):
 // its exact dS is then evaluated later from the unchanged source field.
+// ELBM (elbmLB): alpha with S(f + alpha (f* - f)) = S(f) for one site, from
+// the full populations f and f*, in the arithmetic U of the storage (FP64
+// to 1e-15 relative for FP64 storage; FP32 to its rounding for FP32 and
+// FP16 storage, whose populations carry FP32 rounding already).  With
+// D = f* - f the condition is G(a) = sum f_i phi(a D_i / f_i) - a R = 0,
+// R = sum D_i log1p(D_i / f_i) (sum D = 0 and ln f* linear in the conserved
+// moments remove the two entropies' cancellation); G is convex, G(0) = 0,
+// G(1) <= 0, so the root in [1, alpha_max] (alpha_max: f + a D >= 0) is
+// unique.  Newton with G'(a) = sum D_i log1p(a D_i / f_i) - R, falling back
+// to bisection whenever a step leaves the bracket.  The start point is the
+// root of the series of G to second order in x_i = D_i / f_i,
+// a = 2 + S3 / (3 S2) with Sn = sum f_i x_i^n; near equilibrium (max |x| <
+// 0.1, so alpha_max > 10) the bracket check at alpha_max is skipped.  a = 2
+// when f = f*; alpha_max when the entropy still exceeds S(f) there; -1 when
+// some f_i or f*_i is not positive.
+template <typename L, typename U>
+__device__ __noinline__ U elbm_alpha(const U* f, const U* fs) {
+    constexpr U tol = sizeof(U) == 8 ? U(1e-15) : U(4.0 * 1.1920929e-7);
+    U D[L::Q], R = U(0), amax = U(INFINITY), s2 = U(0), s3 = U(0), xm = U(0);
+    bool moved = false;
+#pragma unroll
+    for (int i = 0; i < L::Q; i++) {
+        if (!(f[i] > U(0)) || !(fs[i] > U(0))) return U(-1);
+        D[i] = fs[i] - f[i];
+        moved |= D[i] != U(0);
+        if (D[i] < U(0)) amax = fmin(amax, f[i] / -D[i]);
+        const U x = D[i] / f[i];
+        R += D[i] * log1p(x);
+        s2 += D[i] * x;
+        s3 += D[i] * x * x;
+        xm = fmax(xm, fabs(x));
+    }
+    if (!moved || !(R > U(0)) || !isfinite(amax)) return U(2);
+    auto G = [&](U a) {
+        U s = U(0);
+#pragma unroll
+        for (int i = 0; i < L::Q; i++) s += f[i] * phi_fn<U>(a * D[i] / f[i]);
+        return s - a * R;
+    };
+    U lo = U(1), hi = amax;
+    if (!(xm < U(0.1)) && G(hi) <= U(0)) return hi;
+    U a = U(2) + s3 / (U(3) * s2);
+    if (!(a > lo && a < hi)) a = U(0.5) * (lo + hi);
+    for (int it = 0; it < 100; it++) {
+        const U g = G(a);
+        if (g <= U(0)) lo = a;
+        else hi = a;
+        U dg = -R;
+#pragma unroll
+        for (int i = 0; i < L::Q; i++) dg += D[i] * log1p(a * D[i] / f[i]);
+        U na = a - g / dg;
+        if (!(na > lo && na < hi)) na = U(0.5) * (lo + hi);
+        const bool done = fabs(na - a) <= tol * a || hi - lo <= tol * hi;
+        a = na;
+        if (done) break;
+    }
+    return a;
+}
+
+// The ELBM step factor -alpha beta of a site from its deviations (kept out
+// of line: the LBGK path does not carry its arrays).
+template <typename L, typename T>
+__device__ __noinline__ T elbm_factor(PopArr<L::Q, T> g, PopArr<L::Q, T> gs, double rho0, double beta) {
+    T fd[L::Q], fsd[L::Q];
+#pragma unroll
+    for (int i = 0; i < L::Q; i++) {
+        fd[i] = g.v[i] + T(L::w(i) * rho0);
+        fsd[i] = gs.v[i] + T(L::w(i) * rho0);
+    }
+    T a = elbm_alpha<L, T>(fd, fsd);
+    if (a < T(0)) a = T(2);   // outside the positive cone: dS = +inf, LBGK
+    return -a * T(beta);
+}
+
 // PROBE = false: the caller guarantees the site is not the probe site.
 template <typename L, typename T, int EQ, bool PROBE = true>
 __device__ __forceinline__ bool update_site(const Params& P, T* g, int x, int y, long long t,
@@ -181,7 +255,19 @@ __device__ __forceinline__ bool update_site(const Params& P, T* g, int x, int y,
     for (int i = 0; i < L::Q; i++) d[i] = g[i] - gs[i];
     const bool pending =
         P.k > 0 && !ds_cleared<L, T, EQ>(d, gs, rho, ux, uy, Par<T>::rho0(P), Par<T>::delta(P));
-    const T nb2 = T(-2) * Par<T>::beta(P);
+    T nb2 = T(-2) * Par<T>::beta(P);
+    if constexpr (EQ == EQ_ENTROPIC) {
+        if (P.elbm) {
+            // f' = f + alpha beta (f* - f) (elbmLB)
+            PopArr<L::Q, T> ga, gsa;
+#pragma unroll
+            for (int i = 0; i < L::Q; i++) {
+                ga.v[i] = g[i];
+                gsa.v[i] = gs[i];
+            }
+            nb2 = elbm_factor<L, T>(ga, gsa, P.rho0, P.beta);
+        }
+    }
 #pragma unroll
     for (int i = 0; i < L::Q; i++) g[i] = dfma<T>(nb2, d[i], g[i]);
     return pending;

@@ -81,6 +81,47 @@ def shock_tube(w, steps=None, precision=lbm.LB_F64, k=None, delta=None, nu=None)
     return r[0], u[0], counts
 
 
+# The nine panels of the shock-tube figure (Sec. 4.1): (equilibrium,
+# collision, nu, Ehrenfests' (k, delta) or None), 400 steps.
+SHOCK_PANELS = {
+    "a": (inputs.EQ_POLY, lbm.LB_COLLISION_LBGK, 1.0 / 30.0, None),
+    "b": (inputs.EQ_ENTROPIC, lbm.LB_COLLISION_LBGK, 1.0 / 30.0, None),
+    "c": (inputs.EQ_ENTROPIC, lbm.LB_COLLISION_ELBM, 1.0 / 30.0, None),
+    "d": (inputs.EQ_POLY, lbm.LB_COLLISION_LBGK, 1e-9, None),
+    "e": (inputs.EQ_ENTROPIC, lbm.LB_COLLISION_LBGK, 1e-9, None),
+    "f": (inputs.EQ_ENTROPIC, lbm.LB_COLLISION_ELBM, 1e-9, None),
+    "g": (inputs.EQ_POLY, lbm.LB_COLLISION_LBGK, 1e-9, (4, 1e-4)),
+    "h": (inputs.EQ_ENTROPIC, lbm.LB_COLLISION_LBGK, 1e-9, (4, 1e-4)),
+    "i": (inputs.EQ_ENTROPIC, lbm.LB_COLLISION_ELBM, 1e-9, (4, 1e-4)),
+}
+
+
+def shock_panel(name, steps=400, precision=lbm.LB_F64):
+    """One panel: (rho, u, Ehrenfests' sites per step) after `steps` steps."""
+    eq, coll, nu, reg = SHOCK_PANELS[name]
+    k, delta = reg if reg else (0, 1e30)
+    w = inputs.shock_tube(nu=nu, delta=delta, k=k, steps=steps, eq=eq)
+    g = lbm.Lattice.from_workload(w, precision=precision)
+    try:
+        g.set_collision(coll)
+        rho, ux, _ = inputs.shock_tube_fields(w)
+        g.init_equilibrium(rho, ux)
+        g.step(steps)
+        g.sync()
+        r, u, _, _ = g.moments()
+        counts = g.counts(steps)
+    finally:
+        g.close()
+    return r[0], u[0], counts
+
+
+def oscillation(rho):
+    """Total variation of rho in excess of that of a monotone profile with the
+    same extremes (0 for a profile without spurious oscillations)."""
+    rho = np.asarray(rho, np.float64)
+    return float(np.abs(np.diff(rho)).sum() - (rho.max() - rho.min()))
+
+
 # --------------------------------------------------------------------------
 # Small cases for profiling (python -m paper_0705_4371_gb300.experiments ...)
 # --------------------------------------------------------------------------

@@ -22,6 +22,7 @@ LB_OK, LB_ERR_ARG, LB_ERR_CUDA, LB_ERR_NONFINITE, LB_ERR_NEWTON, LB_ERR_TIMEOUT,
     LB_ERR_STATE = 0, -1, -2, -3, -4, -5, -6, -7
 
 PRECISIONS = {"f64": LB_F64, "f32": LB_F32, "f32dev": LB_F32_DEV, "f16dev": LB_F16_DEV}
+LB_COLLISION_LBGK, LB_COLLISION_ELBM = 0, 1
 
 
 class LBError(RuntimeError):
@@ -76,6 +77,7 @@ def load(path=None):
         "lb_replay_selection": ([H, vp, vp, ip], ip),
         "lb_mlp_param_count": ([], ip),
         "lb_set_mlp": ([H, vp, ip], ip),
+        "lb_set_collision": ([H, ip], ip),
         "lb_newton_stats": ([H, vp, vp, vp, vp, ip], ip),
         "lb_set_timing": ([H, ip], ip),
         "lb_kernel_times": ([H, vp, vp, vp, vp, ip], ip),
@@ -326,6 +328,9 @@ class Lattice:
         idx = np.concatenate([np.asarray(s, np.int32) for s in selections] + [np.zeros(0, np.int32)])
         idx = np.ascontiguousarray(idx, np.int32)
         _check(self.L.lb_replay_selection(self.h, _ptr(counts), _ptr(idx), len(selections)))
+
+    def set_collision(self, collision):
+        _check(self.L.lb_set_collision(self.h, int(collision)))
 
     def set_mlp(self, params):
         p = np.ascontiguousarray(params, np.float32)
