@@ -14,6 +14,7 @@ from . import build as _build
 D1Q3, D2Q9 = 0, 1
 EQ_POLY, EQ_ENTROPIC, EQ_ENERGY = 0, 1, 2
 BC_BB, BC_FREESLIP, BC_INLET, BC_OUTLET, BC_PERIODIC = 0, 1, 2, 3, 4
+WALL_BOUNCE_BACK, WALL_DIFFUSE = 0, 1
 
 _lib = None
 
@@ -23,7 +24,8 @@ class _Cfg(C.Structure):
                 ("eq", C.c_int), ("beta", C.c_double), ("delta", C.c_double),
                 ("k", C.c_long), ("bc", C.c_int * 4), ("rho_in", C.c_double),
                 ("ux_in", C.c_double), ("uy_in", C.c_double), ("ox0", C.c_int),
-                ("oy0", C.c_int), ("ow", C.c_int), ("oh", C.c_int), ("elbm", C.c_int)]
+                ("oy0", C.c_int), ("ow", C.c_int), ("oh", C.c_int), ("elbm", C.c_int),
+                ("wall", C.c_int)]
 
 
 def lib():
@@ -100,6 +102,7 @@ class Config:
     u_in: tuple = (0.0, 0.0)
     obstacle: tuple = (0, 0, 0, 0)
     elbm: bool = False        # collision (elbmLB) instead of (lbgkLB)
+    wall: int = 0             # rule on the obstacle's faces: WALL_BOUNCE_BACK / WALL_DIFFUSE
 
     @property
     def q(self):
@@ -118,6 +121,7 @@ class Config:
         s.rho_in, s.ux_in, s.uy_in = self.rho_in, self.u_in[0], self.u_in[1]
         s.ox0, s.oy0, s.ow, s.oh = self.obstacle
         s.elbm = 1 if self.elbm else 0
+        s.wall = self.wall
         return s
 
     def solid_mask(self):

@@ -42,6 +42,7 @@ enum { ORA_D1Q3 = 0, ORA_D2Q9 = 1 };
 enum { ORA_EQ_POLY = 0, ORA_EQ_ENTROPIC = 1, ORA_EQ_ENERGY = 2 };
 enum { ORA_BC_BB = 0, ORA_BC_FREESLIP = 1, ORA_BC_INLET = 2,
        ORA_BC_OUTLET = 3, ORA_BC_PERIODIC = 4, ORA_BC_OUTLET_COPY = 5 };
+enum { ORA_WALL_BOUNCE_BACK = 0, ORA_WALL_DIFFUSE = 1 };
 
 /* D1Q3, paper numbering {v1, v2, v3} = {0, -1, +1} (Sec. 4.1): static,
  * left-moving, right-moving.  The weights are not printed; they are read
@@ -502,6 +503,7 @@ typedef struct {
     double rho_in, ux_in, uy_in;   /* inlet state */
     int ox0, oy0, ow, oh;          /* solid rectangle; ow == 0: none */
     int elbm;                      /* collision (elbmLB) instead of (lbgkLB) */
+    int wall;                      /* rule on the rectangle's faces: ORA_WALL_* */
 } ora_cfg;
 
 static int is_solid(const ora_cfg* c, int x, int y)
@@ -530,12 +532,27 @@ static long site(const ora_cfg* c, int x, int y) { return (long)y * c->nx + x; }
  *  - y side FREESLIP: specular reflection, the population (v_x, -v_y) that
  *                   left (x - v_x, y) arrives as (v_x, v_y);
  *  - solid source : half-way bounce-back (the paper leaves the cylinder
- *                   wall rule open; no-slip bounce-back is the reading).
- * The x rule is applied first (inlet/outlet take precedence at corners). */
+ *                   wall rule open; no-slip bounce-back is the reading),
+ *                   or, with wall = ORA_WALL_DIFFUSE, the diffuse kinetic
+ *                   wall of the references of Sec. 4.2 (below).
+ * The x rule is applied first (inlet/outlet take precedence at corners).
+ *
+ * Diffuse wall (Maxwell's diffuse reflection on a wall at rest): the
+ * populations that enter x from the wall are the wall's quasiequilibrium at
+ * rest, f_i(x) = W_i rho_w (every quasiequilibrium of this library is
+ * W_i rho at u = 0), and rho_w makes the wall impermeable: what enters
+ * equals what the wall absorbed, the post-collision populations f'_{-i}(x)
+ * of the same links, so
+ *     f_i(x) = W_i (sum_{j in B} f'_{-j}(x)) / (sum_{j in B} W_j),
+ * B the directions i whose source x - v_i is solid.  On a face every such
+ * link has |v . n| = 1, so the flux weights of the kinetic rule are all one;
+ * at a convex corner B is the one diagonal link (the same rule). */
 static void gather_site(const ora_cfg* c, const double* fp, int x, int y, double* f)
 {
     int L = c->lattice, q = ora_q(L), nx = c->nx, ny = c->ny;
     long N = (long)nx * ny, s0 = site(c, x, y);
+    int wall_link[9] = {0};
+    int nwall = 0;
     for (int i = 0; i < q; i++) {
         int cx = lat_cx(L, i), cy = lat_cy(L, i);
         int sx = x - cx, sy = y - cy;
@@ -581,9 +598,19 @@ static void gather_site(const ora_cfg* c, const double* fp, int x, int y, double
         if (is_solid(c, sx, sy)) {
             int o = lat_find(L, -cx, -cy);
             f[i] = fp[o * N + s0];
+            if (c->wall == ORA_WALL_DIFFUSE) { wall_link[i] = 1; nwall++; }
             continue;
         }
         f[i] = fp[i * N + site(c, sx, sy)];
+    }
+    if (nwall > 0) {
+        /* f[i] holds f'_{-i}(x) on the wall links (read above) */
+        double absorbed = 0.0, wsum = 0.0;
+        for (int i = 0; i < q; i++)
+            if (wall_link[i]) { absorbed += f[i]; wsum += lat_w(L, i); }
+        double rho_w = absorbed / wsum;
+        for (int i = 0; i < q; i++)
+            if (wall_link[i]) f[i] = lat_w(L, i) * rho_w;
     }
 }
 

@@ -46,6 +46,7 @@ class SplitMix64:
 # Boundary kinds (same numbering on both sides of the parity tests).
 # --------------------------------------------------------------------------
 BC_BB, BC_FREESLIP, BC_INLET, BC_OUTLET, BC_PERIODIC, BC_OUTLET_COPY = 0, 1, 2, 3, 4, 5
+WALL_BOUNCE_BACK, WALL_DIFFUSE = 0, 1      # rule on the obstacle's faces
 D1Q3, D2Q9 = 0, 1
 EQ_POLY, EQ_ENTROPIC, EQ_ENERGY, EQ_ENERGY_MLP = 0, 1, 2, 3
 SEED_ENERGY_SAMPLES = 20070531
@@ -71,6 +72,7 @@ class Workload:
     L: int = 0
     seed: int = SEED_CYLINDER
     extra: dict = field(default_factory=dict)
+    wall: int = WALL_BOUNCE_BACK
 
     @property
     def n_sites(self):
@@ -97,13 +99,15 @@ def shock_tube_fields(w: Workload):
 
 
 def cylinder(nx=600, ny=500, L=20, re=1000.0, u_inf=0.05, delta=1e-3, k=16,
-             steps=200000, eq=EQ_POLY, face_x=None, name=None, seed=SEED_CYLINDER, outlet=BC_OUTLET):
+             steps=200000, eq=EQ_POLY, face_x=None, name=None, seed=SEED_CYLINDER, outlet=BC_OUTLET,
+             wall=WALL_BOUNCE_BACK):
     """Square cylinder of side L in a free-slip channel (Sec. 4.2).
 
     Upstream face at x = 5L (face_x), centred in y; inlet at x = 0,
     zero-gradient (quasiequilibrium of the penultimate column) outlet at
     x = nx-1, free-slip walls at y = 0 and y = ny-1.  nu = L u_inf / Re.
-    Probe at (4L, -2L) from the cylinder centre (Sec. 4.2.1).
+    Probe at (4L, -2L) from the cylinder centre (Sec. 4.2.1).  wall: half-way
+    bounce-back or the diffuse kinetic wall on the cylinder's faces.
     """
     fx = 5 * L if face_x is None else face_x
     oy0 = (ny - L) // 2
@@ -112,7 +116,7 @@ def cylinder(nx=600, ny=500, L=20, re=1000.0, u_inf=0.05, delta=1e-3, k=16,
     nu = L * u_inf / re
     return Workload(name or "d2q9_cylinder_%dx%d_L%d_Re%g" % (nx, ny, L, re), D2Q9, nx, ny, eq,
                     nu, delta, k, steps, (BC_INLET, outlet, BC_FREESLIP, BC_FREESLIP),
-                    1.0, (u_inf, 0.0), (fx, oy0, L, L), probe, L, seed)
+                    1.0, (u_inf, 0.0), (fx, oy0, L, L), probe, L, seed, wall=wall)
 
 
 def cylinder_fields(w: Workload, noise=1e-4):

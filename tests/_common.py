@@ -13,7 +13,8 @@ PREC_TOL = {  # relative tolerance of moments after 1000 steps (replayed selecti
 
 def oracle_cfg(w, **over):
     d = dict(lattice=w.lattice, nx=w.nx, ny=w.ny, eq=w.eq, beta=ora.beta_of_nu(w.nu),
-             delta=w.delta, k=w.k, bc=w.bc, rho_in=w.rho_in, u_in=w.u_in, obstacle=w.obstacle)
+             delta=w.delta, k=w.k, bc=w.bc, rho_in=w.rho_in, u_in=w.u_in, obstacle=w.obstacle,
+             wall=w.wall)
     if "nu" in over:
         d["beta"] = ora.beta_of_nu(over.pop("nu"))
     d.update(over)
