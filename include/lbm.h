@@ -88,17 +88,28 @@ enum lb_precision { LB_F64 = 0, LB_F32 = 1, LB_F32_DEV = 2, LB_F16_DEV = 3 };
  *                 y - v_y, or y where that leaves the lattice; x sides only).
  *                 Not in the paper: its equilibrium outlet feeds back the
  *                 reverse flow of vortices leaving the channel.
- * The obstacle is a solid rectangle [x0, x0+w) x [y0, y0+h) (w = 0: none)
- * with half-way bounce-back on its faces; it must keep at least one fluid
- * site to the y walls and two columns to an outlet. */
+ * The obstacle is a solid rectangle [x0, x0+w) x [y0, y0+h) (w = 0: none);
+ * it must keep at least one fluid site to the y walls and two columns to an
+ * outlet.  obstacle_wall selects the rule on its faces (the paper leaves it
+ * open, pointing to kinetic boundary conditions, Sec. 4.2):
+ *   LB_WALL_BOUNCE_BACK  half-way bounce-back, f_i(x) = f'_{-i}(x) (no-slip);
+ *   LB_WALL_DIFFUSE      diffuse kinetic wall at rest (Maxwell's diffuse
+ *                        reflection): the populations entering x from the
+ *                        obstacle are W_i rho_w, rho_w such that they carry
+ *                        exactly the mass f'_{-i}(x) that x sent into it,
+ *                        f_i = W_i sum_B f'_{-j} / sum_B W_j over the set B
+ *                        of x's links into the obstacle.
+ * A zero-initialised struct selects bounce-back.  Any other value: LB_ERR_ARG. */
 enum lb_bc { LB_BB = 0, LB_FREESLIP = 1, LB_INLET_EQ = 2, LB_OUTLET_EQ = 3, LB_PERIODIC = 4,
              LB_OUTLET_COPY = 5 };
+enum lb_wall { LB_WALL_BOUNCE_BACK = 0, LB_WALL_DIFFUSE = 1 };
 
 typedef struct lb_boundaries {
     int kind_x0, kind_x1, kind_y0, kind_y1;
     double rho_in;
     double u_in[2];
     int obstacle_x0, obstacle_y0, obstacle_w, obstacle_h;
+    int obstacle_wall;          /* lb_wall */
 } lb_boundaries;
 
 /* Status codes. */

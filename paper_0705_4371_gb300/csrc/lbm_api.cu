@@ -152,6 +152,7 @@ Params make_params(const lb_handle* h, int src, bool prestream) {
     P.grid_blocks = h->grid_blocks;
     P.tile_counter = h->tile_counter;
     P.elbm = h->elbm ? 1 : 0;
+    P.wall = h->bc.obstacle_wall;
     return P;
 }
 
@@ -393,6 +394,8 @@ int lb_create(int lattice, int nx, int ny, int equilibrium, double nu, double de
         if (!(fabs(b.u_in[0]) < 0.5 && fabs(b.u_in[1]) < 0.5)) return fail(LB_ERR_ARG, "inlet speed too large");
     }
     if (b.obstacle_w < 0 || b.obstacle_h < 0) return fail(LB_ERR_ARG, "negative obstacle size");
+    if (b.obstacle_wall != LB_WALL_BOUNCE_BACK && b.obstacle_wall != LB_WALL_DIFFUSE)
+        return fail(LB_ERR_ARG, "unknown obstacle wall rule %d", b.obstacle_wall);
     if (b.obstacle_w > 0) {
         if (lattice == LB_D1Q3) return fail(LB_ERR_ARG, "no obstacle on D1Q3");
         if (b.obstacle_h <= 0) return fail(LB_ERR_ARG, "obstacle height must be positive");

@@ -61,6 +61,7 @@ static_assert(D2Q9::opp(5) == 7 && D2Q9::opp(6) == 8 && D2Q9::opp(7) == 5 && D2Q
 // ---------------------------------------------------------------------------
 enum : int { EQ_POLY = 0, EQ_ENTROPIC = 1, EQ_ENERGY = 2, EQ_ENERGY_MLP = 3 };
 enum : int { BC_BB = 0, BC_FREESLIP = 1, BC_INLET = 2, BC_OUTLET = 3, BC_PERIODIC = 4, BC_OUTLET_COPY = 5 };
+enum : int { WALL_BOUNCE_BACK = 0, WALL_DIFFUSE = 1 };
 enum : unsigned { ERR_NONFINITE = 1u, ERR_NEWTON = 2u, ERR_TIMEOUT = 4u, ERR_REPLAY = 8u };
 
 struct Params {
@@ -109,6 +110,7 @@ struct Params {
     int grid_blocks;          // persistent grid size (resident blocks x SMs)
     unsigned* tile_counter;   // next tile to hand out (staged shapes)
     int elbm;                 // ELBM collision (elbmLB) instead of LBGK (entropic f* only)
+    int wall;                 // rule on the obstacle's faces: WALL_BOUNCE_BACK / WALL_DIFFUSE
 };
 
 template <int Q, typename T> struct PopArr { T v[Q]; };
@@ -366,9 +368,34 @@ __device__ __forceinline__ unsigned long long ds_key(double d) {
 //           column nx-2 in the same row), BB = own opposite population;
 //   y side: PERIODIC wraps, FREESLIP = population (v_x, -v_y) of (x - v_x, y),
 //           BB = own opposite population;
-//   solid source: own opposite population (half-way bounce-back).
+//   solid source: own opposite population (half-way bounce-back), or with
+//           wall = WALL_DIFFUSE the diffuse kinetic wall (diffuse_wall).
 // The x rule is applied first (inlet and outlet win at corners).
 // ---------------------------------------------------------------------------
+
+// Diffuse kinetic wall at rest (Maxwell's diffuse reflection, the kinetic
+// boundary condition cited in Sec. 4.2): the wall re-emits the mass it
+// absorbed as its rest quasiequilibrium W_i rho_w.  The links in mask
+// (source inside the obstacle) enter holding f'_{-i}(x), the absorbed
+// populations, and leave with
+//   f_i = W_i (sum_{j in mask} f'_{-j}) / (sum_{j in mask} W_j).
+// The same map holds for deviations g = f - W rho0 (the W_i rho0 parts
+// cancel), so it applies to every storage form as it stands.
+template <typename L, typename T>
+__device__ __forceinline__ void diffuse_wall(unsigned mask, T* g) {
+    T absorbed = T(0), wsum = T(0);
+#pragma unroll
+    for (int i = 0; i < L::Q; i++)
+        if ((mask >> i) & 1u) {
+            absorbed += g[i];
+            wsum += T(L::w(i));
+        }
+    const T rho_w = absorbed / wsum;
+#pragma unroll
+    for (int i = 0; i < L::Q; i++)
+        if ((mask >> i) & 1u) g[i] = T(L::w(i)) * rho_w;
+}
+
 template <typename L, typename S>
 __device__ void gather_site(const Params& P, int x, int y, typename Store<S>::T* g) {
     using T = typename Store<S>::T;
@@ -380,6 +407,7 @@ __device__ void gather_site(const Params& P, int x, int y, typename Store<S>::T*
         return;
     }
     bool have_in = false, have_out = false;
+    unsigned wall_mask = 0u;
     T gin[L::Q], gout[L::Q];
 #pragma unroll
     for (int i = 0; i < L::Q; i++) {
@@ -434,10 +462,12 @@ __device__ void gather_site(const Params& P, int x, int y, typename Store<S>::T*
         }
         if (is_solid(P, sx, sy)) {
             g[i] = Store<S>::load(P.src, L::opp(i) * P.plane + s0);
+            if (P.wall == WALL_DIFFUSE) wall_mask |= 1u << i;
             continue;
         }
         g[i] = Store<S>::load(P.src, i * P.plane + (long long)sy * P.nxp + sx);
     }
+    if (wall_mask) diffuse_wall<L, T>(wall_mask, g);
 }
 
 // ---------------------------------------------------------------------------

@@ -868,6 +868,7 @@ __device__ __forceinline__ void gather_site_smem(const Params& P, const S* box, 
         return;
     }
     bool have_in = false, have_out = false;
+    unsigned wall_mask = 0u;
     T gin[L::Q], gout[L::Q];
 #pragma unroll
     for (int i = 0; i < L::Q; i++) {
@@ -907,8 +908,14 @@ __device__ __forceinline__ void gather_site_smem(const Params& P, const S* box, 
             g[i] = kind == BC_FREESLIP ? at(L::mir_y(i), sx, y) : at(L::opp(i), x, y);
             continue;
         }
-        g[i] = is_solid(P, sx, sy) ? at(L::opp(i), x, y) : at(i, sx, sy);
+        if (is_solid(P, sx, sy)) {
+            g[i] = at(L::opp(i), x, y);
+            if (P.wall == WALL_DIFFUSE) wall_mask |= 1u << i;
+        } else {
+            g[i] = at(i, sx, sy);
+        }
     }
+    if (wall_mask) diffuse_wall<L, T>(wall_mask, g);
 }
 
 // The sites of a staged tile that touches a boundary, the obstacle or the

@@ -23,6 +23,7 @@ LB_OK, LB_ERR_ARG, LB_ERR_CUDA, LB_ERR_NONFINITE, LB_ERR_NEWTON, LB_ERR_TIMEOUT,
 
 PRECISIONS = {"f64": LB_F64, "f32": LB_F32, "f32dev": LB_F32_DEV, "f16dev": LB_F16_DEV}
 LB_COLLISION_LBGK, LB_COLLISION_ELBM = 0, 1
+LB_WALL_BOUNCE_BACK, LB_WALL_DIFFUSE = 0, 1
 
 
 class LBError(RuntimeError):
@@ -35,7 +36,7 @@ class lb_boundaries(C.Structure):
     _fields_ = [("kind_x0", C.c_int), ("kind_x1", C.c_int), ("kind_y0", C.c_int),
                 ("kind_y1", C.c_int), ("rho_in", C.c_double), ("u_in", C.c_double * 2),
                 ("obstacle_x0", C.c_int), ("obstacle_y0", C.c_int), ("obstacle_w", C.c_int),
-                ("obstacle_h", C.c_int)]
+                ("obstacle_h", C.c_int), ("obstacle_wall", C.c_int)]
 
 
 class lb_run_desc(C.Structure):
@@ -134,12 +135,13 @@ def _f64(a):
     return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
 
 
-def boundaries(kinds=(LB_BB,) * 4, rho_in=1.0, u_in=(0.0, 0.0), obstacle=(0, 0, 0, 0)):
+def boundaries(kinds=(LB_BB,) * 4, rho_in=1.0, u_in=(0.0, 0.0), obstacle=(0, 0, 0, 0), wall=0):
     b = lb_boundaries()
     b.kind_x0, b.kind_x1, b.kind_y0, b.kind_y1 = kinds
     b.rho_in = rho_in
     b.u_in[0], b.u_in[1] = u_in
     b.obstacle_x0, b.obstacle_y0, b.obstacle_w, b.obstacle_h = obstacle
+    b.obstacle_wall = wall
     return b
 
 
@@ -242,7 +244,7 @@ class Lattice:
         """Create from a paper_0705_4371_gb300.inputs.Workload."""
         p = dict(nu=w.nu, delta=w.delta, k=w.k, equilibrium=w.eq)
         p.update(over)
-        bc = boundaries(w.bc, w.rho_in, w.u_in, w.obstacle)
+        bc = boundaries(w.bc, w.rho_in, w.u_in, w.obstacle, p.get("wall", w.wall))
         return cls(w.lattice, w.nx, w.ny, p["equilibrium"], p["nu"], p["delta"], p["k"], bc, precision,
                    stream)
 
@@ -377,7 +379,7 @@ class Batch:
             d.lattice, d.nx, d.ny = LB_D2Q9, w.nx, w.ny
             d.equilibrium = w.eq if equilibrium is None else equilibrium
             d.nu, d.delta, d.k = w.nu, w.delta, w.k
-            d.bc = boundaries(w.bc, w.rho_in, w.u_in, w.obstacle)
+            d.bc = boundaries(w.bc, w.rho_in, w.u_in, w.obstacle, w.wall)
             d.precision = precision
         h = C.c_void_p()
         _check(self.L.lb_batch_create(descs, n, C.c_void_p(stream) if stream else None, C.byref(h)))
