@@ -333,8 +333,10 @@ int lb_kernel_times(lb_handle* h, double* collide_ms, long long* collide_launche
  * 16 bytes of halo columns; R rows, C columns, STAGES tiles in flight per
  * block): 4 = 8 x 128, STAGES 2 (default);  5 = 4 x 128, STAGES 3;
  * 6 = 8 x 64, STAGES 2 (three blocks per SM).  The energy-constrained forms
- * are built for shapes 1 (their default) and 4 (shapes 5 and 6 run 4).
- * Results do not depend on the shape; only the speed does. */
+ * are built for shapes 0 (1, 8, 2: 128 registers per thread), 1 (2 and 3
+ * run 1) and 4 (5 and 6 run 4); their defaults: 1 for FP64 storage, 4 for
+ * the Newton start and 0 for the network's warm start in FP32 / FP16
+ * storage.  Results do not depend on the shape; only the speed does. */
 int lb_set_tile_shape(lb_handle* h, int shape);
 
 /* Run facts (out: 8 entries): out[0] = Q, out[1] = padded row length

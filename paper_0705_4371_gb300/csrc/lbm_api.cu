@@ -46,9 +46,17 @@ constexpr int kStageCap = 8192;      // candidates staged in shared memory by th
 constexpr int kGraphSteps = 32;      // steps per captured graph (even: buffers return)
 constexpr int kDefaultLog = 65536;
 constexpr int kDefaultTileShape = 4;  // fastest measured on GB300 (staged tiles, 2 in flight)
-// The energy forms are bound by the Newton solve, not by memory: more
-// resident warps (register-fed shape 1) hide its FP64 latency better.
-constexpr int kDefaultTileShapeEnergy = 1;
+// The energy forms are bound by the Newton solve, not by memory (fastest
+// measured on GB300): FP64 storage's FP64 finish wants the most resident warps
+// (register-fed shape 1); the float-float finish of FP32 / FP16 storage runs
+// best in the staged shape, and the network's warm start in the register-fed
+// shape with 128 registers (shape 0), where its fragments spill least.
+int default_tile_shape(int lattice, int eq, int precision) {
+    if (lattice != LB_D2Q9) return 0;
+    if (eq < LB_EQ_ENTROPIC_ENERGY) return kDefaultTileShape;
+    if (precision == LB_F64) return 1;
+    return eq == LB_EQ_ENTROPIC_ENERGY_MLP ? 0 : 4;
+}
 
 size_t storage_bytes(int prec) { return prec == LB_F64 ? 8 : (prec == LB_F16_DEV ? 2 : 4); }
 
@@ -413,8 +421,7 @@ int lb_create(int lattice, int nx, int ny, int equilibrium, double nu, double de
     h->bc = b;
     h->plane = (long long)ny * h->nxp;
     h->probe_x = h->probe_y = -1;
-    h->tile_shape = lattice != LB_D2Q9 ? 0
-                    : equilibrium >= LB_EQ_ENTROPIC_ENERGY ? kDefaultTileShapeEnergy : kDefaultTileShape;
+    h->tile_shape = default_tile_shape(lattice, equilibrium, precision);
     h->ring_cap = kDefaultLog;
     h->replay_t0 = -1;
     if (precision == LB_F64) h->L = launchers_f64(lattice, equilibrium);

@@ -20,6 +20,10 @@
 // member of the family above), takes reciprocals from FP32 seeds refined by
 // Newton-Raphson, and updates b by the Taylor series of e^{-delta} for the
 // tiny FP64 steps.
+// FP32 and FP16 storage round f* to FP32 in the end, and their finishing
+// steps (energy_solve_ff) run in float-float arithmetic instead of FP64:
+// the same steps and the same 1e-12 stop, with about 48 significant bits
+// from FP32 operations only.
 #pragma once
 
 #include "lbm_device.cuh"
@@ -144,12 +148,14 @@ __device__ __forceinline__ double exp_small_neg(double d) {
 // below stop_tol (1e-12, or closer to the rounding floor for FP64 storage).
 // Returns false if the residual did not reach 1e-12 (the site then keeps
 // the last iterate).  a64 (optional): the solution's multipliers in FP64.
-__device__ __forceinline__ bool energy_solve(double rho, double ux, double uy, double th, float* a,
-                                             double* fstar, NewtonCount& nc, double stop_tol,
-                                             double* a64 = nullptr) {
-    // FP32 phase
-    const float tf[3] = {(float)ux, (float)uy, (float)th};
-    float bx = 1.0f, by = 1.0f, bc = 1.0f, rprev = INFINITY;
+// The FP32 phase: Newton on a (FP32) towards the targets tf = (u_x, u_y,
+// 2E / rho); returns the exponentials b = e^{a} of the last iterate.
+__device__ __forceinline__ void energy_phase32(const float* tf, float* a, float& bx, float& by, float& bc,
+                                               NewtonCount& nc) {
+    float rprev = INFINITY;
+    bx = 1.0f;
+    by = 1.0f;
+    bc = 1.0f;
     int it = 0;
     for (;; it++) {
         float q[9], Z, g[3], C[6], d[3];
@@ -169,6 +175,14 @@ __device__ __forceinline__ bool energy_solve(double rho, double ux, double uy, d
         rprev = r;
     }
     nc.it32 += (unsigned)it;
+}
+
+__device__ __forceinline__ bool energy_solve(double rho, double ux, double uy, double th, float* a,
+                                             double* fstar, NewtonCount& nc, double stop_tol,
+                                             double* a64 = nullptr) {
+    const float tf[3] = {(float)ux, (float)uy, (float)th};
+    float bx, by, bc;
+    energy_phase32(tf, a, bx, by, bc, nc);
     // FP64 phase, from the exponentials of the FP32 phase's last iterate
     const double tg[3] = {ux, uy, th};
     double b[3] = {(double)bx, (double)by, (double)bc};
@@ -215,6 +229,155 @@ __device__ __forceinline__ bool energy_solve(double rho, double ux, double uy, d
     const double s = rho * iz;
 #pragma unroll
     for (int i = 0; i < 9; i++) fstar[i] = s * q[i];
+    return ok;
+}
+
+// ---------------------------------------------------------------------------
+// Float-float arithmetic: a value is the unevaluated sum hi + lo of two
+// floats with |lo| <= ulp(hi) / 2 (about 48 significant bits).  Built on the
+// error-free transformations two-sum (Knuth) and two-product (by one fused
+// multiply-add); the addition is the "sloppy" form of Dekker's algorithm
+// (its error is relative to |a| + |b|, which is what the residual sums
+// below need).  The library is compiled without multiply-add contraction,
+// so every rounding written here happens as written.
+// ---------------------------------------------------------------------------
+struct ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ ff ff_fast_two_sum(float a, float b) {   // |a| >= |b| or a == 0
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+    const ff s = ff_two_sum(a.hi, b.hi);
+    return ff_fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
+__device__ __forceinline__ ff ff_scale(ff a, float p2) { return {a.hi * p2, a.lo * p2}; }   // p2 a power of two
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return ff_fast_two_sum(p, e);
+}
+__device__ __forceinline__ ff ff_mul_f(ff a, float b) {
+    const float p = a.hi * b;
+    float e = fmaf(a.hi, b, -p);
+    e = fmaf(a.lo, b, e);
+    return ff_fast_two_sum(p, e);
+}
+// 1 / a: the correctly rounded FP32 reciprocal r plus one Newton-Raphson
+// correction r (1 - a r), whose leading part fma(-a.hi, r, 1) is exact.
+__device__ __forceinline__ ff ff_recip(ff a) {
+    const float r = __frcp_rn(a.hi);
+    float e = fmaf(-a.hi, r, 1.0f);
+    e = fmaf(-a.lo, r, e);
+    return ff_fast_two_sum(r, r * e);
+}
+// e^{-d} for |d| < 2^-10: 1 - d exactly as a float-float, plus the Taylor
+// terms d^2/2 - d^3/6 + d^4/24 (below 2^-21) in FP32.
+__device__ __forceinline__ ff ff_exp_small_neg(float d) {
+    const ff s = ff_two_sum(1.0f, -d);
+    const float tail = d * d * fmaf(-d, fmaf(-d, 1.0f / 24.0f, 1.0f / 6.0f), 0.5f);
+    return ff_fast_two_sum(s.hi, s.lo + tail);
+}
+
+// 36 q_i (weights 16, 4, 1: exact in FP32) from b = e^{a} and 1/bx, 1/by.
+__device__ __forceinline__ void energy_q_ff(ff bx, ff by, ff bc, ff ibx, ff iby, ff* q) {
+    const ff bc2 = ff_mul(bc, bc);
+    q[0] = {16.0f, 0.0f};
+    q[1] = ff_scale(ff_mul(bx, bc), 4.0f);
+    q[2] = ff_scale(ff_mul(by, bc), 4.0f);
+    q[3] = ff_scale(ff_mul(ibx, bc), 4.0f);
+    q[4] = ff_scale(ff_mul(iby, bc), 4.0f);
+    q[5] = ff_mul(ff_mul(bx, by), bc2);
+    q[6] = ff_mul(ff_mul(ibx, by), bc2);
+    q[7] = ff_mul(ff_mul(ibx, iby), bc2);
+    q[8] = ff_mul(ff_mul(bx, iby), bc2);
+}
+
+// Residual g = E[m'] - t from q (any common scale); returns max |g| and 1/Z.
+__device__ __forceinline__ float energy_residual_ff(const ff* q, const ff* tgt, ff& iz, ff* g) {
+    const ff qa = ff_add(ff_add(q[1], q[2]), ff_add(q[3], q[4]));
+    const ff qd = ff_add(ff_add(q[5], q[6]), ff_add(q[7], q[8]));
+    iz = ff_recip(ff_add(q[0], ff_add(qa, qd)));
+    const ff sx = ff_add(ff_sub(q[1], q[3]), ff_sub(ff_add(q[5], q[8]), ff_add(q[6], q[7])));
+    const ff sy = ff_add(ff_sub(q[2], q[4]), ff_sub(ff_add(q[5], q[6]), ff_add(q[7], q[8])));
+    const ff sc = ff_add(qa, ff_scale(qd, 2.0f));
+    g[0] = ff_sub(ff_mul(sx, iz), tgt[0]);
+    g[1] = ff_sub(ff_mul(sy, iz), tgt[1]);
+    g[2] = ff_sub(ff_mul(sc, iz), tgt[2]);
+    return fmaxf(fmaxf(fabsf(g[0].hi), fabsf(g[1].hi)), fabsf(g[2].hi));
+}
+
+// Energy-constrained quasiequilibrium for FP32 / FP16 storage from the FP32
+// moments (rho, j, 2E): the FP32 phase, then Newton steps with the residual
+// in float-float (covariance and 3 x 3 solve in FP32, as in energy_solve)
+// until the residual is at or below 1e-12.  Writes the deviations
+// gs_i = f*_i - W_i rho0, rounded once to FP32.  Returns false if the
+// residual did not reach 1e-12 (the site keeps the last iterate).
+__device__ __forceinline__ bool energy_solve_ff(float rho, float jx, float jy, float e2, float rho0, float* a,
+                                                float* gs, NewtonCount& nc) {
+    const ff ir = ff_recip({rho, 0.0f});
+    const ff tg[3] = {ff_mul_f(ir, jx), ff_mul_f(ir, jy), ff_mul_f(ir, e2)};
+    const float tf[3] = {tg[0].hi, tg[1].hi, tg[2].hi};
+    float bx, by, bc;
+    energy_phase32(tf, a, bx, by, bc, nc);
+    ff b[3] = {{bx, 0.0f}, {by, 0.0f}, {bc, 0.0f}};
+    ff ib[2] = {ff_recip(b[0]), ff_recip(b[1])};
+    ff q[9], iz = {1.0f, 0.0f};
+    bool ok = false;
+    int it = 0;
+    for (;; it++) {
+        ff g[3];
+        energy_q_ff(b[0], b[1], b[2], ib[0], ib[1], q);
+        const float r = energy_residual_ff(q, tg, iz, g);
+        ok = r <= (float)kNewtonTol;
+        if (ok || it == kNewton64Max) break;
+        float qf[9], Cf[6], gf[3], df[3], Zf, unused[3];
+        const float zero[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int i = 0; i < 9; i++) qf[i] = q[i].hi;
+        energy_terms<float>(qf, zero, Zf, unused, Cf);
+        gf[0] = g[0].hi;
+        gf[1] = g[1].hi;
+        gf[2] = g[2].hi;
+        if (!spd3_solve(Cf, gf, df)) break;
+        const float dm = fmaxf(fmaxf(fabsf(df[0]), fabsf(df[1])), fabsf(df[2]));
+        if (dm < 0x1p-10f) {
+            for (int j = 0; j < 3; j++) b[j] = ff_mul(b[j], ff_exp_small_neg(df[j]));
+        } else {
+            // a long step (the FP32 phase stopped early): damped; any positive
+            // b is a member of the family, so the new b need not be exact
+            const float sc = dm > 0.5f ? 0.5f / dm : 1.0f;
+            for (int j = 0; j < 3; j++) b[j] = {b[j].hi * expf(-sc * df[j]), 0.0f};
+        }
+        ib[0] = ff_recip(b[0]);
+        ib[1] = ff_recip(b[1]);
+    }
+    nc.it64 += (unsigned)it;
+    nc.sites += 1u;
+    if (!ok) nc.fails += 1u;
+    // f*_i = rho q_i / Z; W_i as float-float constants for the deviation
+    const ff s = ff_mul_f(iz, rho);
+    constexpr double w[3] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 36.0};
+    constexpr float whi[3] = {(float)w[0], (float)w[1], (float)w[2]};
+    constexpr float wlo[3] = {(float)(w[0] - (double)whi[0]), (float)(w[1] - (double)whi[1]),
+                              (float)(w[2] - (double)whi[2])};
+#pragma unroll
+    for (int i = 0; i < 9; i++) {
+        const int k = i == 0 ? 0 : (i < 5 ? 1 : 2);
+        const ff d = ff_sub(ff_mul(s, q[i]), ff_mul_f({whi[k], wlo[k]}, rho0));
+        gs[i] = d.hi + d.lo;
+    }
     return ok;
 }
 

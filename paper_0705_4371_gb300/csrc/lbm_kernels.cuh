@@ -42,20 +42,36 @@ __device__ __forceinline__ void equilibrium(const Params& P, T drho, T rho, T ux
 template <typename T, int EQ>
 __device__ __forceinline__ void equilibrium_energy(const Params& P, T rho, T jx, T jy, T e2, T* gs,
                                                    NewtonCount& nc, const float* a0 = nullptr) {
-    const double r = (double)rho, ir = recip64(r);
-    const double ux = (double)jx * ir, uy = (double)jy * ir;
-    float a[3] = {3.0f * (float)ux, 3.0f * (float)uy, 0.0f};
-    if (a0) {
-        a[0] = a0[0];
-        a[1] = a0[1];
-        a[2] = a0[2];
-    }
-    double fs[9];
-    const double stop = sizeof(T) == 8 ? 4e-15 : kNewtonTol;
-    energy_solve(r, ux, uy, (double)e2 * ir, a, fs, nc, stop);
-    const double rho0 = P.rho0;
+    if constexpr (sizeof(T) == 4) {
+        // FP32 / FP16 storage: the float-float finish (no FP64 work)
+        float a[3];
+        if (a0) {
+            a[0] = a0[0];
+            a[1] = a0[1];
+            a[2] = a0[2];
+        } else {
+            const float ir = __frcp_rn(rho);
+            a[0] = 3.0f * (jx * ir);
+            a[1] = 3.0f * (jy * ir);
+            a[2] = 0.0f;
+        }
+        energy_solve_ff(rho, jx, jy, e2, Par<T>::rho0(P), a, gs, nc);
+    } else {
+        // FP64 storage: FP64 finish to 4e-15 (the FP64 parity bound)
+        const double r = (double)rho, ir = recip64(r);
+        const double ux = (double)jx * ir, uy = (double)jy * ir;
+        float a[3] = {3.0f * (float)ux, 3.0f * (float)uy, 0.0f};
+        if (a0) {
+            a[0] = a0[0];
+            a[1] = a0[1];
+            a[2] = a0[2];
+        }
+        double fs[9];
+        energy_solve(r, ux, uy, (double)e2 * ir, a, fs, nc, 4e-15);
+        const double rho0 = P.rho0;
 #pragma unroll
-    for (int i = 0; i < 9; i++) gs[i] = (T)(fs[i] - D2Q9::w(i) * rho0);
+        for (int i = 0; i < 9; i++) gs[i] = (T)(fs[i] - D2Q9::w(i) * rho0);
+    }
 }
 
 template <typename L, typename T>
@@ -1353,8 +1369,11 @@ template <typename L, typename S, int EQ>
 struct LaunchImpl {
     static cudaError_t collide(const Params& P, int shape, const void* tmap, cudaStream_t st) {
         if constexpr (L::Q == 9 && EQ >= EQ_ENERGY) {
-            // the energy forms are built for one register-fed and one staged shape
+            // the energy forms are built for two register-fed shapes (0: two
+            // resident blocks, 128 registers per thread; 1-3: four, 64) and
+            // one staged shape
             if (shape >= 4) return launch_d2q9_tma<S, EQ, 8, 2>(P, tmap, st);
+            if (shape == 0) return launch_d2q9<S, EQ, 1, 8, 2>(P, st);
             return launch_d2q9<S, EQ, 1, 8, 4>(P, st);
         } else if constexpr (L::Q == 9) {
             switch (shape) {
@@ -1379,6 +1398,7 @@ struct LaunchImpl {
         *per_sm = 1;
         if constexpr (L::Q == 9 && EQ >= EQ_ENERGY) {
             if (shape >= 4) return setup_d2q9_tma<S, EQ, 8, 2>(per_sm);
+            if (shape == 0) return occupancy_d2q9<S, EQ, 1, 8, 2>(per_sm);
             return occupancy_d2q9<S, EQ, 1, 8, 4>(per_sm);
         } else if constexpr (L::Q == 9) {
             switch (shape) {
