@@ -186,55 +186,123 @@ __device__ __noinline__ double delta_s_fp64(PopArr<L::Q, T> g, double rho0) {
 // the full populations f and f*, in the arithmetic U of the storage (FP64
 // to 1e-15 relative for FP64 storage; FP32 to its rounding for FP32 and
 // FP16 storage, whose populations carry FP32 rounding already).  With
-// D = f* - f the condition is G(a) = sum f_i phi(a D_i / f_i) - a R = 0,
-// R = sum D_i log1p(D_i / f_i) (sum D = 0 and ln f* linear in the conserved
-// moments remove the two entropies' cancellation); G is convex, G(0) = 0,
-// G(1) <= 0, so the root in [1, alpha_max] (alpha_max: f + a D >= 0) is
-// unique.  Newton with G'(a) = sum D_i log1p(a D_i / f_i) - R, falling back
-// to bisection whenever a step leaves the bracket.  The start point is the
-// root of the series of G to second order in x_i = D_i / f_i,
-// a = 2 + S3 / (3 S2) with Sn = sum f_i x_i^n; near equilibrium (max |x| <
-// 0.1, so alpha_max > 10) the bracket check at alpha_max is skipped.  a = 2
-// when f = f*; alpha_max when the entropy still exceeds S(f) there; -1 when
-// some f_i or f*_i is not positive.
+// D = f* - f and x_i = D_i / f_i the condition is
+// G(a) = sum f_i phi(a x_i) - a R = 0, R = sum D_i log1p(x_i) (sum D = 0 and
+// ln f* linear in the conserved moments remove the two entropies'
+// cancellation); G is convex, G(0) = 0, G(1) <= 0, so the root in
+// [1, alpha_max] (alpha_max = 1 / max(-x_i): f + a D >= 0) is unique.
+// Newton with G'(a) = sum D_i log1p(a x_i) - R, falling back to bisection
+// whenever a step leaves the bracket.  The start point is the root of the
+// series of G to second order in x, a = 2 + S3 / (3 S2) with
+// Sn = sum f_i x_i^n; near equilibrium (max |x| < 0.1, so alpha_max > 10)
+// the bracket check at alpha_max is skipped.  Stop: FP64 when a step or the
+// bracket falls below 1e-15 relative; FP32 once a step is below 3e-4
+// relative (Newton converges quadratically with G''/G' ~ 1/2 here, so the
+// result of that step is within about 1e-7 of the root, FP32's rounding;
+// iterating further in FP32 only chases the rounding noise of G, and the
+// slowest lane holds its whole warp).  a = 2 when f = f*; alpha_max when
+// the entropy still exceeds S(f) there; -1 when some f_i or f*_i is not
+// positive.
+// FP32 near equilibrium (max |x| < 0.1, almost every site) takes a branch-
+// free path instead: with Sn = sum f_i x_i^n, the series of G / a is
+//   P(a) = sum_{n>=2} (-1)^n Sn (a^{n-1}/n - 1)/(n - 1),
+// whose terms beyond n = 10 are below 1e-9 S2 for |a x| <= 0.21 (the root
+// lies within 2 +- max|x| / 3 there), far below FP32's rounding of P (about
+// 1e-7 S2); three Newton steps on P from the series root 2 + S3 / (3 S2)
+// reach the FP32 root (P is almost linear: P' ~ S2 / 2).  No logarithm and
+// no data-dependent loop, so the lanes of a warp stay together.
+template <int Q, typename U>
+__device__ __forceinline__ U elbm_alpha_series(const U* D, const U* x) {
+    // c_n = (-1)^n Sn / (n - 1), n = 2..10, with Sn = sum D_i x_i^{n-1}
+    U c[11];
+#pragma unroll
+    for (int n = 0; n < 11; n++) c[n] = U(0);
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        U t = D[i] * x[i];
+#pragma unroll
+        for (int n = 2; n <= 10; n++) {
+            c[n] += t;
+            t *= x[i];
+        }
+    }
+    if (!(c[2] > U(0))) return U(2);
+    const U a0 = U(2) + c[3] / (U(3) * c[2]);   // 2 + S3 / (3 S2)
+    // P(a) = a B(a) - sum c_n with B(a) = sum b_n a^{n-2}, b_n = c_n / n;
+    // P'(a) = sum d_n a^{n-2}, d_n = c_n (n - 1) / n
+    U b[11], d[11], sumc = U(0);
+#pragma unroll
+    for (int n = 2; n <= 10; n++) {
+        const U cn = ((n & 1) ? -c[n] : c[n]) * U(1.0 / (n - 1));
+        sumc += cn;
+        b[n] = cn * U(1.0 / n);
+        d[n] = cn * U((n - 1.0) / n);
+    }
+    U a = a0;
+#pragma unroll
+    for (int it = 0; it < 3; it++) {
+        U B = b[10], dP = d[10];
+#pragma unroll
+        for (int n = 9; n >= 2; n--) {
+            B = dfma<U>(B, a, b[n]);
+            dP = dfma<U>(dP, a, d[n]);
+        }
+        a -= (a * B - sumc) / dP;
+    }
+    return a;
+}
+
 template <typename L, typename U>
 __device__ __noinline__ U elbm_alpha(const U* f, const U* fs) {
-    constexpr U tol = sizeof(U) == 8 ? U(1e-15) : U(4.0 * 1.1920929e-7);
-    U D[L::Q], R = U(0), amax = U(INFINITY), s2 = U(0), s3 = U(0), xm = U(0);
-    bool moved = false;
+    constexpr bool fp64 = sizeof(U) == 8;
+    constexpr U step_tol = fp64 ? U(1e-15) : U(3e-4);
+    constexpr U bracket_tol = fp64 ? U(1e-15) : U(4.0 * 1.1920929e-7);
+    constexpr int max_it = fp64 ? 100 : 40;
+    U D[L::Q], x[L::Q], R = U(0), xneg = U(0), s2 = U(0), s3 = U(0), xm = U(0);
+    bool moved = false, positive = true;
 #pragma unroll
     for (int i = 0; i < L::Q; i++) {
-        if (!(f[i] > U(0)) || !(fs[i] > U(0))) return U(-1);
+        positive &= f[i] > U(0) && fs[i] > U(0);
         D[i] = fs[i] - f[i];
         moved |= D[i] != U(0);
-        if (D[i] < U(0)) amax = fmin(amax, f[i] / -D[i]);
-        const U x = D[i] / f[i];
-        R += D[i] * log1p(x);
-        s2 += D[i] * x;
-        s3 += D[i] * x * x;
-        xm = fmax(xm, fabs(x));
+        x[i] = D[i] / f[i];
+        xneg = fmax(xneg, -x[i]);
+        xm = fmax(xm, fabs(x[i]));
     }
-    if (!moved || !(R > U(0)) || !isfinite(amax)) return U(2);
+    if (!positive) return U(-1);
+    if (!moved || !(xneg > U(0))) return U(2);
+    if constexpr (!fp64) {
+        if (xm < U(0.1)) return elbm_alpha_series<L::Q, U>(D, x);
+    }
+#pragma unroll
+    for (int i = 0; i < L::Q; i++) {
+        R += D[i] * log1p(x[i]);
+        s2 += D[i] * x[i];
+        s3 += D[i] * x[i] * x[i];
+    }
+    if (!(R > U(0))) return U(2);
+    const U amax = U(1) / xneg;
     auto G = [&](U a) {
         U s = U(0);
 #pragma unroll
-        for (int i = 0; i < L::Q; i++) s += f[i] * phi_fn<U>(a * D[i] / f[i]);
+        for (int i = 0; i < L::Q; i++) s += f[i] * phi_fn<U>(a * x[i]);
         return s - a * R;
     };
     U lo = U(1), hi = amax;
     if (!(xm < U(0.1)) && G(hi) <= U(0)) return hi;
     U a = U(2) + s3 / (U(3) * s2);
     if (!(a > lo && a < hi)) a = U(0.5) * (lo + hi);
-    for (int it = 0; it < 100; it++) {
+    for (int it = 0; it < max_it; it++) {
         const U g = G(a);
         if (g <= U(0)) lo = a;
         else hi = a;
         U dg = -R;
 #pragma unroll
-        for (int i = 0; i < L::Q; i++) dg += D[i] * log1p(a * D[i] / f[i]);
+        for (int i = 0; i < L::Q; i++) dg += D[i] * log1p(a * x[i]);
         U na = a - g / dg;
-        if (!(na > lo && na < hi)) na = U(0.5) * (lo + hi);
-        const bool done = fabs(na - a) <= tol * a || hi - lo <= tol * hi;
+        const bool newton = na > lo && na < hi;
+        if (!newton) na = U(0.5) * (lo + hi);
+        const bool done = (newton && fabs(na - a) <= step_tol * a) || hi - lo <= bracket_tol * hi;
         a = na;
         if (done) break;
     }
@@ -244,16 +312,16 @@ __device__ __noinline__ U elbm_alpha(const U* f, const U* fs) {
 // The ELBM step factor -alpha beta of a site from its deviations (kept out
 // of line: the LBGK path does not carry its arrays).
 template <typename L, typename T>
-__device__ __noinline__ T elbm_factor(PopArr<L::Q, T> g, PopArr<L::Q, T> gs, double rho0, double beta) {
+__device__ __noinline__ T elbm_factor(PopArr<L::Q, T> g, PopArr<L::Q, T> gs, T rho0, T beta) {
     T fd[L::Q], fsd[L::Q];
 #pragma unroll
     for (int i = 0; i < L::Q; i++) {
-        fd[i] = g.v[i] + T(L::w(i) * rho0);
-        fsd[i] = gs.v[i] + T(L::w(i) * rho0);
+        fd[i] = g.v[i] + T(L::w(i)) * rho0;
+        fsd[i] = gs.v[i] + T(L::w(i)) * rho0;
     }
     T a = elbm_alpha<L, T>(fd, fsd);
     if (a < T(0)) a = T(2);   // outside the positive cone: dS = +inf, LBGK
-    return -a * T(beta);
+    return -a * beta;
 }
 
 // PROBE = false: the caller guarantees the site is not the probe site.
@@ -281,7 +349,7 @@ __device__ __forceinline__ bool update_site(const Params& P, T* g, int x, int y,
                 ga.v[i] = g[i];
                 gsa.v[i] = gs[i];
             }
-            nb2 = elbm_factor<L, T>(ga, gsa, P.rho0, P.beta);
+            nb2 = elbm_factor<L, T>(ga, gsa, Par<T>::rho0(P), Par<T>::beta(P));
         }
     }
 #pragma unroll

@@ -150,6 +150,23 @@ def energy_case(eq, steps=3, nx=512, ny=256):
               % (eq, kt["collide_ms"] / kt["collide_launches"], s[0] / s[2], s[1] / s[2]))
 
 
+def elbm_case(steps=44, nx=1024, ny=512, precision=lbm.LB_F32):
+    """The entropic cylinder (L = ny/16, Re 20000, k 16) with the ELBM
+    collision: 40 steps, then `steps - 40` directly launched (timed) steps.
+    Prints the kernel time per step."""
+    w = inputs.cylinder(nx, ny, ny // 16, 20000.0, eq=inputs.EQ_ENTROPIC)
+    with lbm.Lattice.from_workload(w, precision=precision) as g:
+        g.set_collision(lbm.LB_COLLISION_ELBM)
+        g.init_equilibrium(*inputs.cylinder_fields(w, noise=1e-2))
+        g.step(40)
+        g.set_timing(True)
+        g.step(max(1, steps - 40))
+        g.sync()
+        kt = g.kernel_times()
+        ms = kt["collide_ms"] / kt["collide_launches"]
+        print("elbm case %d x %d: %.4f ms per step, %.0f MLUPS" % (nx, ny, ms, w.n_sites / ms / 1e3))
+
+
 def batch_case(nruns=24, steps=44, variant=0):
     """The first nruns runs of the 64-run batch (FP32 deviation storage):
     40 steps, then `steps - 40` directly launched (timed) steps."""
@@ -168,11 +185,15 @@ def batch_case(nruns=24, steps=44, variant=0):
 
 def main(argv=None):
     import argparse
-    ap = argparse.ArgumentParser(description="small GPU cases of the learned and batched forms")
+    ap = argparse.ArgumentParser(description="small GPU cases of the learned and batched forms and of ELBM")
     sub = ap.add_subparsers(dest="case", required=True)
     e = sub.add_parser("energy")
     e.add_argument("--eq", type=int, default=2)
     e.add_argument("--steps", type=int, default=3)
+    el = sub.add_parser("elbm")
+    el.add_argument("--steps", type=int, default=44)
+    el.add_argument("--nx", type=int, default=1024)
+    el.add_argument("--ny", type=int, default=512)
     b = sub.add_parser("batch")
     b.add_argument("--runs", type=int, default=24)
     b.add_argument("--steps", type=int, default=44)
@@ -181,6 +202,8 @@ def main(argv=None):
     lbm.load()
     if a.case == "energy":
         energy_case(a.eq, a.steps)
+    elif a.case == "elbm":
+        elbm_case(a.steps, a.nx, a.ny)
     else:
         batch_case(a.runs, a.steps, a.variant)
 
