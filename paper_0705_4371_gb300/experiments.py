@@ -127,10 +127,11 @@ def oscillation(rho):
 # --------------------------------------------------------------------------
 
 def energy_case(eq, steps=3, nx=512, ny=256):
-    """The energy-constrained cylinder (Re 5000, k 64) with the smooth energy
-    pattern, FP32 storage, `steps` directly launched steps; eq 3 first trains
-    a network on 2e6 samples.  Prints the kernel time and Newton iterations."""
-    w = inputs.cylinder(nx, ny, 16, 5000.0, k=64, eq=inputs.EQ_ENERGY)
+    """The energy-constrained cylinder (L = ny/16, Re 5000, k 64) with the
+    smooth energy pattern, FP32 storage, `steps` directly launched steps; eq 3
+    first trains a network on 2e6 samples.  Prints the kernel time and Newton
+    iterations."""
+    w = inputs.cylinder(nx, ny, ny // 16, 5000.0, k=64, eq=inputs.EQ_ENERGY)
     rho, ux, uy = inputs.cylinder_fields(w, noise=1e-2)
     with lbm.Lattice.from_workload(w, precision=lbm.LB_F64) as iso:
         iso.init_equilibrium(rho, ux, uy)
@@ -146,7 +147,7 @@ def energy_case(eq, steps=3, nx=512, ny=256):
         g.sync()
         kt = g.kernel_times()
         s = g.newton_stats()
-        print("energy case eq %d: %.4f ms per launch, FP32 / FP64 Newton iterations per site %.3f / %.3f"
+        print("energy case eq %d: %.4f ms per launch, FP32 / high-precision Newton iterations per site %.3f / %.3f"
               % (eq, kt["collide_ms"] / kt["collide_launches"], s[0] / s[2], s[1] / s[2]))
 
 
@@ -190,6 +191,8 @@ def main(argv=None):
     e = sub.add_parser("energy")
     e.add_argument("--eq", type=int, default=2)
     e.add_argument("--steps", type=int, default=3)
+    e.add_argument("--nx", type=int, default=512)
+    e.add_argument("--ny", type=int, default=256)
     el = sub.add_parser("elbm")
     el.add_argument("--steps", type=int, default=44)
     el.add_argument("--nx", type=int, default=1024)
@@ -201,7 +204,7 @@ def main(argv=None):
     a = ap.parse_args(argv)
     lbm.load()
     if a.case == "energy":
-        energy_case(a.eq, a.steps)
+        energy_case(a.eq, a.steps, a.nx, a.ny)
     elif a.case == "elbm":
         elbm_case(a.steps, a.nx, a.ny)
     else:
