@@ -396,7 +396,7 @@ def learned_form(args, stream):
                          "ms_per_step": round(fms / args.learned_steps, 4),
                          "collide_ms": round(k2["collide_ms"] / max(k2["collide_launches"], 1), 4),
                          "newton_fp32_it_per_site": round(it32 / max(sites, 1), 4),
-                         "newton_fp64_it_per_site": round(it64 / max(sites, 1), 4),
+                         "newton_finish_it_per_site": round(it64 / max(sites, 1), 4),
                          "newton_fails": int(fails), "steps": args.learned_steps}
     out["speedup"] = round(out["mlp_warm_start"]["MLUPS"] / out["newton"]["MLUPS"], 4)
     return out
