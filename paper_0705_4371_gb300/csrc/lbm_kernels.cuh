@@ -777,11 +777,10 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_collide_d2q9(const __grid_
     const int per_block = (tiles + gridDim.x - 1) / gridDim.x;
     const int t0 = blockIdx.x * per_block;
     const int t1 = min(t0 + per_block, tiles);
-    int w = t0 + warp;
-    int y = w / tiles_x, xt = w - y * tiles_x;
     bool nonfinite = false;
     NewtonCount nc = {0, 0, 0, 0};
-    for (; w < t1; w += WARPS) {
+    // one row tile of 32 * VEC sites: row y, tile column xt
+    auto do_tile = [&](int y, int xt) {
         const int x0 = xt * TX;
         const int xs = x0 + lane * VEC;
         if (!P.prestream && tile_interior<TX>(P, x0, y)) {
@@ -842,8 +841,38 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_collide_d2q9(const __grid_
                 warp_pend(P, fs, (r & 2) != 0, (unsigned)(y * P.nx + x));
             }
         }
-        xt += WARPS;
-        while (xt >= tiles_x) { xt -= tiles_x; y++; }
+    };
+    if constexpr (EQ < EQ_ENERGY) {
+        int w = t0 + warp;
+        int y = w / tiles_x, xt = w - y * tiles_x;
+        for (; w < t1; w += WARPS) {
+            do_tile(y, xt);
+            xt += WARPS;
+            while (xt >= tiles_x) { xt -= tiles_x; y++; }
+        }
+    } else {
+        // The energy forms go in rounds of one tile per warp and resolve the
+        // block's pending sites once its list could not take another round's
+        // (as the staged kernel does): a start far from equilibrium then
+        // cannot overflow many sites to the global list, which the last
+        // block alone resolves.  npend is read between two barriers with no
+        // writes in between, so the branch is uniform.
+        const int rounds = t1 > t0 ? (t1 - t0 + WARPS - 1) / WARPS : 0;
+        for (int r = 0; r < rounds; r++) {
+            const int w = t0 + r * WARPS + warp;
+            if (w < t1) {
+                const int y = w / tiles_x;
+                do_tile(y, w - y * tiles_x);
+            }
+            __syncthreads();
+            if (fs.npend > (unsigned)(kPend - TX * WARPS)) {
+                resolve_list<L, S, EQ>(P, (int)min(fs.npend, (unsigned)kPend),
+                                       [&](int j) { return fs.pend[j]; });
+                __syncthreads();
+                if (threadIdx.x == 0) fs.npend = 0;
+                __syncthreads();
+            }
+        }
     }
     if (nonfinite) atomicOr(P.err, ERR_NONFINITE);
     if constexpr (EQ >= EQ_ENERGY) flush_newton(P, nc);

@@ -123,3 +123,24 @@ def test_energy_run_replayed_selection(lbm, prec):
     it32, it64, sites, fails = g.newton_stats()
     assert fails == 0
     print("Newton iterations per site: FP32 %.2f FP64 %.2f" % (it32 / sites, it64 / sites))
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16dev", "f64"])
+def test_energy_tile_shapes_give_identical_results(lbm, prec):
+    # the energy forms' register-fed shapes (0: 128 registers, 1: 64) and the
+    # staged shape 4 run the same per-site arithmetic; a noisy start puts
+    # many sites near delta, so the pending lists fill and drain in the loop
+    w = energy_cylinder(nx=328, ny=150, L=12, delta=1e-7, k=64)
+    rho, ux, uy, e2 = energy_fields(w, 21, noise=2e-2)
+    states = {}
+    for shape in (0, 1, 4):
+        g = lbm.Lattice.from_workload(w, precision=lbm.PRECISIONS[prec])
+        g.set_tile_shape(shape)
+        g.init_equilibrium(rho, ux, uy, e2)
+        g.step(12)
+        states[shape] = (g.get_state(), g.counts(12))
+        g.close()
+    for shape in (1, 4):
+        assert np.array_equal(states[0][0], states[shape][0]), shape
+        assert np.array_equal(states[0][1], states[shape][1]), shape
+    assert states[0][1].sum() > 0
