@@ -534,18 +534,18 @@ def run_reference(args):
     from oracle import core as ora
     w_full = workload_by_name(args.workload)
     # calibrate the oracle's rate on the 1/8-scaled layout, then take the
-    # largest layout of the same workload family whose K + W steps fit the
-    # time budget
+    # largest layout of the same workload family whose K + W steps fit in
+    # --ref-seconds
     cal = inputs.workload_c3_scaled()
     o, cfg, f = _oracle_setup(cal)
     t0 = time.perf_counter()
     o.run(cfg, f, 3, log_selection=False)
     rate = cal.n_sites * 3 / (time.perf_counter() - t0)
-    budget = args.ref_seconds / max(1, args.steps + args.warmup)
+    per_step_s = args.ref_seconds / max(1, args.steps + args.warmup)
     cands = [w_full] + [inputs.cylinder(w_full.nx // s, w_full.ny // s, max(4, w_full.L // s),
                                         20000.0, name="%s_scaled_1_%d" % (w_full.name, s))
                         for s in (2, 4, 8, 16, 32)]
-    w = next((c for c in cands if c.n_sites / rate <= budget), cands[-1])
+    w = next((c for c in cands if c.n_sites / rate <= per_step_s), cands[-1])
     o, cfg, f = _oracle_setup(w)
     for _ in range(args.warmup):
         f, _ = o.run(cfg, f, 1, log_selection=False)
