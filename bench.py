@@ -35,10 +35,12 @@ PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_collide_d2q9_cylinder4096x20
 
 
 def kernel_source_hash():
+    """Hash of the sources the stream-collide kernels are compiled from (the
+    device headers and their instantiation units; not the host API)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_0705_4371_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
+        if name.endswith((".cuh", ".h")) or (name.startswith("lbm_kernels_") and name.endswith(".cu")):
             with open(os.path.join(csrc, name), "rb") as fh:
                 h.update(name.encode())
                 h.update(fh.read())
