@@ -113,6 +113,11 @@ struct lb_handle {
     float* mlp;
     bool mlp_set;
     bool elbm;                // ELBM collision (elbmLB)
+    // device staging of FP64 host fields (state import/export, initial
+    // fields): allocated on first use and kept, since mapping hundreds of MB
+    // per call costs more than the copy itself
+    double* stage;
+    size_t stage_bytes;
     unsigned long long* newton_stats;
     // completion ticket of the stream-collide blocks; tile shape of K1
     unsigned* ticket;
@@ -352,7 +357,7 @@ void lb_destroy(lb_handle* h) {
     void* ptrs[] = {h->buf[0], h->buf[1], h->cand_key, h->cand_idx, h->cand_count, h->sel_idx,
                     h->sel_count, h->count_ring, h->probe_ring, h->d_step, h->d_err, h->replay_cnt,
                     h->replay_off, h->replay_idx, h->mlp, h->newton_stats, h->ticket,
-                    h->pend_idx, h->pend_count, h->tile_counter};
+                    h->pend_idx, h->pend_count, h->tile_counter, h->stage};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_err) cudaFreeHost(h->h_err);
@@ -501,6 +506,22 @@ int lb_create(int lattice, int nx, int ny, int equilibrium, double nu, double de
     return LB_OK;
 }
 
+// The handle's staging buffer, at least `bytes` long (the previous calls that
+// used it have synchronised with the stream).
+static int staging(lb_handle* h, size_t bytes, double** out) {
+    if (h->stage_bytes < bytes) {
+        if (h->stage) cudaFree(h->stage);
+        h->stage = nullptr;
+        h->stage_bytes = 0;
+        // room for every use at once: Q population planes or 4 field planes
+        const size_t full = (size_t)std::max(h->Q, 4) * h->nx * h->ny * sizeof(double);
+        CK(cudaMalloc(&h->stage, std::max(bytes, full)));
+        h->stage_bytes = std::max(bytes, full);
+    }
+    *out = h->stage;
+    return LB_OK;
+}
+
 int lb_init_equilibrium(lb_handle* h, const double* rho, const double* ux, const double* uy,
                         const double* e2) {
     if (!h || !rho || !ux) return fail(LB_ERR_ARG, "NULL argument");
@@ -510,14 +531,13 @@ int lb_init_equilibrium(lb_handle* h, const double* rho, const double* ux, const
             return fail(LB_ERR_ARG, "init field out of range at site %lld", i);
     double* d = nullptr;
     const size_t nb = N * sizeof(double);
-    CK(cudaMallocAsync(&d, 4 * nb, h->stream));
+    if (int rc = staging(h, 4 * nb, &d)) return rc;
     CK(cudaMemcpyAsync(d, rho, nb, cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemcpyAsync(d + N, ux, nb, cudaMemcpyHostToDevice, h->stream));
     if (uy) CK(cudaMemcpyAsync(d + 2 * N, uy, nb, cudaMemcpyHostToDevice, h->stream));
     if (e2) CK(cudaMemcpyAsync(d + 3 * N, e2, nb, cudaMemcpyHostToDevice, h->stream));
     Params P = make_params(h, 1 - h->cur, true);   // dst = buf[cur]
     CK(h->L.init_eq(P, d, d + N, uy ? d + 2 * N : nullptr, e2 ? d + 3 * N : nullptr, h->stream));
-    CK(cudaFreeAsync(d, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     h->prestream = true;
     return LB_OK;
@@ -528,11 +548,10 @@ int lb_set_state(lb_handle* h, const double* f) {
     const long long N = (long long)h->nx * h->ny;
     const size_t nb = (size_t)h->Q * N * sizeof(double);
     double* d = nullptr;
-    CK(cudaMallocAsync(&d, nb, h->stream));
+    if (int rc = staging(h, nb, &d)) return rc;
     CK(cudaMemcpyAsync(d, f, nb, cudaMemcpyHostToDevice, h->stream));
     Params P = make_params(h, 1 - h->cur, true);
     CK(h->L.import_state(P, d, h->stream));
-    CK(cudaFreeAsync(d, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     h->prestream = true;
     return LB_OK;
@@ -550,7 +569,7 @@ static int export_fields(lb_handle* h, int mode, double* o0, double* o1, double*
     }
     double* d = nullptr;
     const size_t per = (size_t)N * sizeof(double) * (mode == 0 ? h->Q : 1);
-    CK(cudaMallocAsync(&d, per * (mode == 1 ? 4 : 1), h->stream));
+    if (int rc = staging(h, per * (mode == 1 ? 4 : 1), &d)) return rc;
     Params P = make_params(h, h->cur, h->prestream);
     double* d0 = d;
     double* d1 = (mode == 1 && o1) ? d + N : nullptr;
@@ -560,7 +579,6 @@ static int export_fields(lb_handle* h, int mode, double* o0, double* o1, double*
     double* dd[4] = {d0, d1, d2, d3};
     for (int i = 0; i < (mode == 1 ? 4 : 1); i++)
         if (outs[i] && dd[i]) CK(cudaMemcpyAsync(outs[i], dd[i], per, cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaFreeAsync(d, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     (void)nout;
     return LB_OK;

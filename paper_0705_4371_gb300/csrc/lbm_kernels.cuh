@@ -1362,6 +1362,13 @@ __global__ void k_import(const __grid_constant__ Params P, const double* f) {
     const int x = (int)(sid % P.nx), y = (int)(sid / P.nx);
     const long long o = (long long)y * P.nxp + x;
     const bool solid = is_solid(P, x, y);
+    if (P.rho0 == 0.0) {
+        // plain storage: a conversion only (no FP64 arithmetic)
+#pragma unroll
+        for (int i = 0; i < L::Q; i++)
+            Store<S>::store(P.dst, i * P.plane + o, (typename Store<S>::T)(solid ? 0.0 : f[i * N + sid]));
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < L::Q; i++) {
         const double v = solid ? 0.0 : f[i * N + sid] - L::w(i) * P.rho0;
@@ -1396,19 +1403,52 @@ __global__ void k_export(const __grid_constant__ Params P, int mode, double* o0,
 #pragma unroll
         for (int i = 0; i < L::Q; i++) o0[i * N + sid] = (double)g[i] + L::w(i) * P.rho0;
     } else if (mode == 1) {
-        double rho = 0, jx = 0, jy = 0, e2 = 0;
+        if constexpr (sizeof(T) == 4) {
+            // FP32 / FP16 storage: the sums of the stored values in float-float
+            // (exact for these nine floats) and u = j / rho by one corrected
+            // FP32 quotient, so that only the conversions to FP64 touch the FP64
+            // pipe; the rho0 parts (sum W = 1, sum W v = 0, sum W |v|^2) are added
+            // in FP64 at the end.
+            ff r = {0.0f, 0.0f}, jx = {0.0f, 0.0f}, jy = {0.0f, 0.0f}, e = {0.0f, 0.0f};
 #pragma unroll
-        for (int i = 0; i < L::Q; i++) {
-            const double f = (double)g[i] + L::w(i) * P.rho0;
-            rho += f;
-            jx += L::cx(i) * f;
-            jy += L::cy(i) * f;
-            e2 += (L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i)) * f;
+            for (int i = 0; i < L::Q; i++) {
+                const ff gi = {g[i], 0.0f};
+                r = ff_add(r, gi);
+                if (L::cx(i) == 1) jx = ff_add(jx, gi);
+                if (L::cx(i) == -1) jx = ff_sub(jx, gi);
+                if (L::cy(i) == 1) jy = ff_add(jy, gi);
+                if (L::cy(i) == -1) jy = ff_sub(jy, gi);
+                const int c2 = L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i);
+                if (c2 > 0) e = ff_add(e, ff_scale(gi, (float)c2));
+            }
+            const double rho = (P.rho0 + (double)r.hi) + (double)r.lo;
+            const ff rf = ff_add({P.rho0f, 0.0f}, r);
+            const ff ir = ff_recip(rf);
+            o0[sid] = rho;
+            if (o1) {
+                const ff u = ff_mul(jx, ir);
+                o1[sid] = (double)u.hi + (double)u.lo;
+            }
+            if (o2) {
+                const ff v = ff_mul(jy, ir);
+                o2[sid] = (double)v.hi + (double)v.lo;
+            }
+            if (o3) o3[sid] = (L::sum_w_c2 * P.rho0 + (double)e.hi) + (double)e.lo;
+        } else {
+            double rho = 0, jx = 0, jy = 0, e2 = 0;
+#pragma unroll
+            for (int i = 0; i < L::Q; i++) {
+                const double f = (double)g[i] + L::w(i) * P.rho0;
+                rho += f;
+                jx += L::cx(i) * f;
+                jy += L::cy(i) * f;
+                e2 += (L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i)) * f;
+            }
+            o0[sid] = rho;
+            if (o1) o1[sid] = jx / rho;
+            if (o2) o2[sid] = jy / rho;
+            if (o3) o3[sid] = e2;
         }
-        o0[sid] = rho;
-        if (o1) o1[sid] = jx / rho;
-        if (o2) o2[sid] = jy / rho;
-        if (o3) o3[sid] = e2;
     } else {
         T gs[L::Q], rho, ux, uy;
         site_equilibrium<L, T, EQ>(P, g, gs, rho, ux, uy);
