@@ -54,7 +54,9 @@ enum lb_lattice { LB_D1Q3 = 0, LB_D2Q9 = 1 };
  *   LB_EQ_ENTROPIC_ENERGY      entropic with the energy constraint as well,
  *                   M = (rho, rho u1, rho u2, 2E) ((argmax), Lagrange form of
  *                   Sec. 3.3), solved per site by Newton from the polynomial
- *                   start point (FP32 iterations, FP64 final updates);
+ *                   start point (FP32 iterations, then finishing steps to a
+ *                   residual of 1e-12 with the residual in float-float for
+ *                   FP32 / FP16 storage, in FP64 for FP64 storage);
  *   LB_EQ_ENTROPIC_ENERGY_MLP  as above, Newton warm-started by the 4-64-64-4
  *                   network loaded with lb_set_mlp (BF16 tensor cores). */
 enum lb_equilibrium {
@@ -310,7 +312,9 @@ int lb_mlp_train(float* params, const float* feat, const float* dmu, long long n
                  double lr0, double lr1, float* loss_log, void* cuda_stream);
 
 /* Newton statistics of the energy forms since the last reset: total
- * FP32 and FP64 iterations, sites solved, and sites that missed 1e-12. */
+ * FP32 iterations, finishing iterations (float-float for FP32 / FP16
+ * storage, FP64 for FP64 storage), sites solved, and sites that missed
+ * 1e-12. */
 int lb_newton_stats(lb_handle* h, long long* it32, long long* it64, long long* sites,
                     long long* fails, int reset);
 
