@@ -407,10 +407,12 @@ int lb_batch_set_variant(lb_batch* b, int variant);
 
 /* Autotuner: when cache_path (may be NULL) holds an entry for this device
  * and batch (device name, SM count, storage, equilibrium, run sizes), its
- * variant is used; otherwise every variant is timed over `steps` steps
- * (CUDA events), the fastest is chosen and written to the cache (a JSON
- * object).  Timing advances every run by 1 + variants x (steps + 2) steps
- * (all variants compute identical results).  variant_out may be NULL. */
+ * variant is used; otherwise every variant is timed as it runs in
+ * production, over `steps` steps rounded up to whole graphs of 32 (CUDA
+ * events around the graph replays, after one warm-up graph), the fastest is
+ * chosen and written to the cache (a JSON object).  Timing advances every
+ * run by 1 + variants x 32 x (1 + ceil(steps / 32)) steps (all variants
+ * compute identical results).  variant_out may be NULL. */
 int lb_batch_autotune(lb_batch* b, int steps, const char* cache_path, int* variant_out);
 
 /* Per-launch CUDA events (graphs are not used while enabled), summed by

@@ -333,7 +333,12 @@ void run_advance(lb_handle* h, long long n) {
 }
 
 int run_queue_step(lb_handle* h, int src, bool prestream, cudaStream_t st) {
-    const Params P = make_params(h, src, prestream);
+    Params P = make_params(h, src, prestream);
+    // beside the batch's other runs (concurrent graph branches) a small run
+    // keeps to few blocks, at least four 1024-site tiles each, instead of
+    // spreading over the whole GPU as it does when stepped alone
+    const long long cap = std::max(1ll, ((long long)h->nx * h->ny + 4095) / 4096);
+    P.grid_blocks = (int)std::min((long long)P.grid_blocks, cap);
     CK(h->L.collide(P, h->tile_shape, &h->tmap[src], st));
     return LB_OK;
 }

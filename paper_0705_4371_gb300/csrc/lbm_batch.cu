@@ -512,25 +512,34 @@ int lb_batch_autotune(lb_batch* b, int steps, const char* cache_path, int* varia
         if (variant_out) *variant_out = v;
         return LB_OK;
     }
+    // Each strategy is timed as it runs in production: whole graphs of
+    // kBatchGraphSteps steps (steps rounded up to whole graphs), after one
+    // graph of warm-up, with events on the batch's stream.
     double ms[kBatchVariants];
     const bool timing = b->timing;
+    b->timing = false;
+    const int graphs = std::max(1, (steps + kBatchGraphSteps - 1) / kBatchGraphSteps);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        b->timing = timing;
+        return fail(LB_ERR_CUDA, "cudaEventCreate failed");
+    }
     int rc = lb_batch_step(b, 1);   // leaves a fresh state's first step out of the timing
     for (int t = 0; t < kBatchVariants && rc == LB_OK; t++) {
         rc = lb_batch_set_variant(b, t);
+        if (rc == LB_OK) rc = lb_batch_step(b, kBatchGraphSteps);   // warm-up (builds the graph)
         if (rc != LB_OK) break;
-        rc = lb_batch_step(b, 2);   // warm-up
-        if (rc != LB_OK) break;
-        double acc = 0.0;
-        long long cnt = 0;
-        b->timing = true;
-        sum_times(b);
-        b->acc_ms = 0.0;
-        b->acc_n = 0;
-        rc = lb_batch_step(b, steps);
-        if (rc == LB_OK) rc = lb_batch_kernel_times(b, &acc, &cnt, 1);
-        b->timing = timing;
-        ms[t] = cnt > 0 ? acc / (double)cnt : 1e30;
+        float el = 0.0f;
+        if (cudaEventRecord(e0, b->stream) != cudaSuccess) rc = fail(LB_ERR_CUDA, "cudaEventRecord failed");
+        if (rc == LB_OK) rc = lb_batch_step(b, graphs * kBatchGraphSteps);
+        if (rc == LB_OK && (cudaEventRecord(e1, b->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                            cudaEventElapsedTime(&el, e0, e1) != cudaSuccess))
+            rc = fail(LB_ERR_CUDA, "autotune timing failed");
+        ms[t] = rc == LB_OK ? (double)el / (graphs * kBatchGraphSteps) : 1e30;
     }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
     b->timing = timing;
     if (rc != LB_OK) return rc;
     v = (int)(std::min_element(ms, ms + kBatchVariants) - ms);

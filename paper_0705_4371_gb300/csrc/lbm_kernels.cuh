@@ -211,17 +211,17 @@ __device__ __noinline__ double delta_s_fp64(PopArr<L::Q, T> g, double rho0) {
 // 1e-7 S2); three Newton steps on P from the series root 2 + S3 / (3 S2)
 // reach the FP32 root (P is almost linear: P' ~ S2 / 2).  No logarithm and
 // no data-dependent loop, so the lanes of a warp stay together.
-template <int Q, typename U>
+template <int Q, int NT, typename U>
 __device__ __forceinline__ U elbm_alpha_series(const U* D, const U* x) {
-    // c_n = (-1)^n Sn / (n - 1), n = 2..10, with Sn = sum D_i x_i^{n-1}
-    U c[11];
+    // c_n = (-1)^n Sn / (n - 1), n = 2..NT, with Sn = sum D_i x_i^{n-1}
+    U c[NT + 1];
 #pragma unroll
-    for (int n = 0; n < 11; n++) c[n] = U(0);
+    for (int n = 0; n <= NT; n++) c[n] = U(0);
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         U t = D[i] * x[i];
 #pragma unroll
-        for (int n = 2; n <= 10; n++) {
+        for (int n = 2; n <= NT; n++) {
             c[n] += t;
             t *= x[i];
         }
@@ -230,9 +230,9 @@ __device__ __forceinline__ U elbm_alpha_series(const U* D, const U* x) {
     const U a0 = U(2) + c[3] / (U(3) * c[2]);   // 2 + S3 / (3 S2)
     // P(a) = a B(a) - sum c_n with B(a) = sum b_n a^{n-2}, b_n = c_n / n;
     // P'(a) = sum d_n a^{n-2}, d_n = c_n (n - 1) / n
-    U b[11], d[11], sumc = U(0);
+    U b[NT + 1], d[NT + 1], sumc = U(0);
 #pragma unroll
-    for (int n = 2; n <= 10; n++) {
+    for (int n = 2; n <= NT; n++) {
         const U cn = ((n & 1) ? -c[n] : c[n]) * U(1.0 / (n - 1));
         sumc += cn;
         b[n] = cn * U(1.0 / n);
@@ -241,9 +241,9 @@ __device__ __forceinline__ U elbm_alpha_series(const U* D, const U* x) {
     U a = a0;
 #pragma unroll
     for (int it = 0; it < 3; it++) {
-        U B = b[10], dP = d[10];
+        U B = b[NT], dP = d[NT];
 #pragma unroll
-        for (int n = 9; n >= 2; n--) {
+        for (int n = NT - 1; n >= 2; n--) {
             B = dfma<U>(B, a, b[n]);
             dP = dfma<U>(dP, a, d[n]);
         }
@@ -272,7 +272,7 @@ __device__ __noinline__ U elbm_alpha(const U* f, const U* fs) {
     if (!positive) return U(-1);
     if (!moved || !(xneg > U(0))) return U(2);
     if constexpr (!fp64) {
-        if (xm < U(0.1)) return elbm_alpha_series<L::Q, U>(D, x);
+        if (xm < U(0.1)) return elbm_alpha_series<L::Q, 10, U>(D, x);
     }
 #pragma unroll
     for (int i = 0; i < L::Q; i++) {
@@ -1463,12 +1463,13 @@ __global__ void k_export(const __grid_constant__ Params P, int mode, double* o0,
 // and of the staged kernel (rows x columns per block tile, tiles in flight):
 //   4: 8 x 128, 2     5: 4 x 128, 3     6: 8 x 64, 2
 // The persistent grid is (resident blocks per SM) x (SM count), from the
-// occupancy calculator, capped by the number of row tiles.
+// occupancy calculator, capped by the number of tiles (small grids then
+// spread over as many SMs as they have tiles: their step is latency-bound).
 // ---------------------------------------------------------------------------
 template <typename S, int EQ, int VEC, int WARPS, int MINB>
 cudaError_t launch_d2q9(const Params& P, cudaStream_t st) {
     const long long tiles = (long long)((P.nx + 32 * VEC - 1) / (32 * VEC)) * P.ny;
-    const long long want = (tiles + 4 * WARPS - 1) / (4 * WARPS);   // at least 4 tiles per warp
+    const long long want = (tiles + WARPS - 1) / WARPS;   // at least one tile per warp
     const unsigned blocks = (unsigned)std::max(1ll, std::min(want, (long long)P.grid_blocks));
     k_collide_d2q9<S, EQ, VEC, WARPS, MINB><<<blocks, 32 * WARPS, 0, st>>>(P);
     return cudaGetLastError();
@@ -1485,7 +1486,7 @@ template <typename S, int EQ, int R, int STAGES, int TX = kTmaTX>
 cudaError_t launch_d2q9_tma(const Params& P, const void* tmap, cudaStream_t st) {
     constexpr size_t smem = tma_smem_bytes<S, R, STAGES, EQ, TX>();
     const long long tiles = (long long)((P.nx + TX - 1) / TX) * ((P.ny + R - 1) / R);
-    const long long want = (tiles + 3) / 4;   // at least 4 tiles per block
+    const long long want = tiles;   // at least one tile per block
     const unsigned blocks = (unsigned)std::max(1ll, std::min(want, (long long)P.grid_blocks));
     k_collide_d2q9_tma<S, EQ, R, STAGES, TX><<<blocks, 32 * R, smem, st>>>(
         P, *static_cast<const CUtensorMap*>(tmap));
