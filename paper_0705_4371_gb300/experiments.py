@@ -184,9 +184,25 @@ def batch_case(nruns=24, steps=44, variant=0):
         print("batch case: %d runs, %d sites, %.4f ms per step" % (nruns, b.info()["sites"], kt["ms"] / kt["launches"]))
 
 
+def paper_cylinder(re, k=10, delta=1e-3, wall=inputs.WALL_BOUNCE_BACK, steps=None, L=20,
+                   eq=inputs.EQ_ENTROPIC, precision=lbm.LB_F32):
+    """The cylinder as Sec. 4.2 sets it up: 30L x 25L channel (600 x 500 at
+    L = 20), cylinder centre at 10.5L, u_inf = 0.05, entropic f*, run to
+    t_max = 1250 L / u_inf (5e5 steps at L = 20), zero-gradient outflow, the
+    Strouhal number from the probe at (4L, -2L) over the final quarter."""
+    w = inputs.cylinder(30 * L, 25 * L, L, re, k=k, delta=delta, eq=eq, face_x=10 * L,
+                        outlet=inputs.BC_OUTLET_COPY, wall=wall)
+    n = int(1250 * L / w.u_in[0]) if steps is None else steps
+    r = cylinder_run(w, n, precision=precision, chunk=10000)
+    r.pop("probe_tail", None)
+    r.update({"wall": wall, "eq": eq, "L": L})
+    return r
+
+
 def main(argv=None):
     import argparse
-    ap = argparse.ArgumentParser(description="small GPU cases of the learned and batched forms and of ELBM")
+    ap = argparse.ArgumentParser(description="GPU cases: profiling cases of the learned and batched forms "
+                                             "and of ELBM; the paper's cylinder runs")
     sub = ap.add_subparsers(dest="case", required=True)
     e = sub.add_parser("energy")
     e.add_argument("--eq", type=int, default=2)
@@ -197,6 +213,12 @@ def main(argv=None):
     el.add_argument("--steps", type=int, default=44)
     el.add_argument("--nx", type=int, default=1024)
     el.add_argument("--ny", type=int, default=512)
+    c = sub.add_parser("cylinder")
+    c.add_argument("--re", type=float, nargs="+", default=[500.0, 1000.0, 2000.0, 5000.0, 10000.0, 20000.0])
+    c.add_argument("--k", type=int, default=10)
+    c.add_argument("--delta", type=float, default=1e-3)
+    c.add_argument("--wall", choices=["bounce-back", "diffuse"], default="bounce-back")
+    c.add_argument("--steps", type=int, default=None)
     b = sub.add_parser("batch")
     b.add_argument("--runs", type=int, default=24)
     b.add_argument("--steps", type=int, default=44)
@@ -207,6 +229,11 @@ def main(argv=None):
         energy_case(a.eq, a.steps, a.nx, a.ny)
     elif a.case == "elbm":
         elbm_case(a.steps, a.nx, a.ny)
+    elif a.case == "cylinder":
+        import json
+        wall = inputs.WALL_DIFFUSE if a.wall == "diffuse" else inputs.WALL_BOUNCE_BACK
+        for re in a.re:
+            print(json.dumps(paper_cylinder(re, a.k, a.delta, wall, a.steps)), flush=True)
     else:
         batch_case(a.runs, a.steps, a.variant)
 
