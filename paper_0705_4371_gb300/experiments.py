@@ -12,7 +12,7 @@ from . import inputs, lbm, strouhal
 
 
 def cylinder_run(w, steps, precision=lbm.LB_F32, k=None, delta=None, noise=1e-4, chunk=2000,
-                 tail=0.25, stream=None):
+                 tail=0.25, stream=None, collision=lbm.LB_COLLISION_LBGK):
     """Run the square-cylinder workload w for `steps` steps.  Returns a dict
     with the step at which the run became non-finite (None if it did not),
     the Strouhal number of the probe signal's final `tail` fraction (None if
@@ -28,6 +28,8 @@ def cylinder_run(w, steps, precision=lbm.LB_F32, k=None, delta=None, noise=1e-4,
            "re": w.L * w.u_in[0] / w.nu}
     g = lbm.Lattice.from_workload(w, precision=precision, stream=stream, **over)
     try:
+        if collision != lbm.LB_COLLISION_LBGK:
+            g.set_collision(collision)
         g.set_log_capacity(max(keep, min(steps, 65536)))
         g.set_probe(*w.probe)
         g.init_equilibrium(*inputs.cylinder_fields(w, noise=noise))
@@ -185,7 +187,7 @@ def batch_case(nruns=24, steps=44, variant=0):
 
 
 def paper_cylinder(re, k=10, delta=1e-3, wall=inputs.WALL_BOUNCE_BACK, steps=None, L=20,
-                   eq=inputs.EQ_ENTROPIC, precision=lbm.LB_F32):
+                   eq=inputs.EQ_ENTROPIC, precision=lbm.LB_F32, collision=lbm.LB_COLLISION_LBGK):
     """The cylinder as Sec. 4.2 sets it up: 30L x 25L channel (600 x 500 at
     L = 20), cylinder centre at 10.5L, u_inf = 0.05, entropic f*, run to
     t_max = 1250 L / u_inf (5e5 steps at L = 20), zero-gradient outflow, the
@@ -193,9 +195,9 @@ def paper_cylinder(re, k=10, delta=1e-3, wall=inputs.WALL_BOUNCE_BACK, steps=Non
     w = inputs.cylinder(30 * L, 25 * L, L, re, k=k, delta=delta, eq=eq, face_x=10 * L,
                         outlet=inputs.BC_OUTLET_COPY, wall=wall)
     n = int(1250 * L / w.u_in[0]) if steps is None else steps
-    r = cylinder_run(w, n, precision=precision, chunk=10000)
+    r = cylinder_run(w, n, precision=precision, chunk=10000, collision=collision)
     r.pop("probe_tail", None)
-    r.update({"wall": wall, "eq": eq, "L": L})
+    r.update({"wall": wall, "eq": eq, "L": L, "collision": collision})
     return r
 
 
@@ -219,6 +221,7 @@ def main(argv=None):
     c.add_argument("--delta", type=float, default=1e-3)
     c.add_argument("--wall", choices=["bounce-back", "diffuse"], default="bounce-back")
     c.add_argument("--steps", type=int, default=None)
+    c.add_argument("--collision", choices=["lbgk", "elbm"], default="lbgk")
     b = sub.add_parser("batch")
     b.add_argument("--runs", type=int, default=24)
     b.add_argument("--steps", type=int, default=44)
@@ -233,7 +236,8 @@ def main(argv=None):
         import json
         wall = inputs.WALL_DIFFUSE if a.wall == "diffuse" else inputs.WALL_BOUNCE_BACK
         for re in a.re:
-            print(json.dumps(paper_cylinder(re, a.k, a.delta, wall, a.steps)), flush=True)
+            coll = lbm.LB_COLLISION_ELBM if a.collision == "elbm" else lbm.LB_COLLISION_LBGK
+            print(json.dumps(paper_cylinder(re, a.k, a.delta, wall, a.steps, collision=coll)), flush=True)
     else:
         batch_case(a.runs, a.steps, a.variant)
 

@@ -56,3 +56,12 @@ def test_shock_tube_runner_conserves_mass(lbm):
     rho, u, counts = experiments.shock_tube(w)
     assert abs(rho.sum() - 0.75 * w.nx) < 1e-9 * w.nx
     assert counts.size == w.steps and counts.max() <= w.k
+
+
+def test_paper_cylinder_setup_runs(lbm):
+    # the Sec. 4.2 layout at L = 8 (240 x 200), a short run of each collision
+    from paper_0705_4371_gb300 import experiments
+    for coll in (lbm.LB_COLLISION_LBGK, lbm.LB_COLLISION_ELBM):
+        r = experiments.paper_cylinder(1000.0, k=4, delta=1e-4, steps=3000, L=8, collision=coll)
+        assert r["diverged_at"] is None and r["steps"] == 3000
+        assert r["collision"] == coll and r["strouhal"] is not None
