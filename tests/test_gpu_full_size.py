@@ -1,12 +1,13 @@
-"""Parity at the full size of the roofline workload (square cylinder
+"""Parity at full size.  The roofline workload (square cylinder
 4096 x 2048, L = 128, Re = 20000, delta = 1e-3, k = 16) in the launch
 configuration the benchmark times (default staged tile shape, steps replayed
 as CUDA graphs of 32): the oracle takes whole steps of the full grid from
 the GPU's exported state (OpenMP over the host cores, well under a second
 per step), and the GPU replays the oracle's selections so that both sides
-take the same Ehrenfests' steps.  A second threshold (delta = 1e-6) makes
-the selection itself work at this size; the selected sets are compared
-exactly."""
+take the same Ehrenfests' steps; the GPU's own FP64 selection is compared
+with the oracle's exactly.  The other workloads at their full sizes: the
+600 x 500 channel (c2), the energy-constrained 2048 x 1024 run (c4), and
+four runs of the 64-run batch stepped as one graph (c5)."""
 import numpy as np
 import pytest
 
@@ -83,3 +84,84 @@ def test_full_size_delta_s_matches_the_oracle(lbm):
         assert np.array_equal(np.flatnonzero(ds_g[~m] > w.delta), np.flatnonzero(ds_o[~m] > w.delta))
     finally:
         g.close()
+
+
+def test_full_size_c2_cylinder_matches_the_oracle(lbm):
+    # 600 x 500, L = 20, polynomial f*, zero-gradient outflow, Re 1000, plain
+    # FP32: 100 steps from the spun-up state with the oracle's selections
+    w = inputs.workload_c2(1000.0)
+    cfg = oracle_cfg(w)
+    g = _spun_up(lbm, w, "f32")
+    try:
+        f0 = g.get_state()
+        fo, log = ora.run(cfg, f0.copy(), 100)
+        g.set_state(f0)
+        g.replay_selection(log.selected)
+        g.step(100)
+        g.sync()
+        e = rel_err(g.get_state(), fo, cfg.solid_mask())
+        print("c2 full size, 100 steps: max |df| / max |f| %.3g, Ehrenfests' sites %d"
+              % (e, log.counts.sum()))
+        assert e < 2e-5
+    finally:
+        g.close()
+
+
+def test_full_size_c4_energy_form_matches_the_oracle(lbm):
+    # 2048 x 1024, L = 64, Re 5000, k = 64, energy-constrained f* (Newton on
+    # every site of both sides), FP32 storage, the benchmark's energy pattern
+    w = inputs.workload_c4()
+    cfg = oracle_cfg(w)
+    rho, ux, uy = inputs.cylinder_fields(w)
+    with lbm.Lattice.from_workload(w, precision=lbm.LB_F64) as iso:
+        iso.init_equilibrium(rho, ux, uy)
+        e2 = iso.moments()[3] * inputs.energy_factor(w)
+    g = lbm.Lattice.from_workload(w, precision=lbm.LB_F32)
+    try:
+        g.init_equilibrium(rho, ux, uy, e2)
+        g.step(20)
+        g.sync()
+        f0 = g.get_state()
+        fo, log = ora.run(cfg, f0.copy(), 2)
+        g.set_state(f0)
+        g.replay_selection(log.selected)
+        g.step(2)
+        g.sync()
+        e = rel_err(g.get_state(), fo, cfg.solid_mask())
+        print("c4 full size, 2 steps: max |df| / max |f| %.3g" % e)
+        assert e < 2e-6
+        assert g.newton_stats()[3] == 0
+    finally:
+        g.close()
+
+
+@pytest.mark.parametrize("variant", [0, 2])
+def test_full_size_c5_batch_runs_match_the_oracle(lbm, variant):
+    # the 64-run batch (FP32 deviation storage) stepped as one graph of 32
+    # steps; four of its runs (the smallest, the largest and two others)
+    # against whole oracle steps from the same exported states
+    ws = inputs.workload_c5()
+    sizes = [w.nx * w.ny for w in ws]
+    picks = sorted({int(np.argmin(sizes)), int(np.argmax(sizes)), 7, 40})
+    b = lbm.Batch(ws, precision=lbm.LB_F32_DEV)
+    try:
+        b.set_variant(variant)
+        for r, w in enumerate(ws):
+            b.run(r).init_equilibrium(*inputs.cylinder_fields(w))
+        b.step(64)
+        b.sync()
+        f0 = {r: b.run(r).get_state() for r in picks}
+        for r in picks:
+            b.run(r).set_state(f0[r])     # the same state, now on both sides
+        b.step(32)
+        b.sync()
+        for r in picks:
+            cfg = oracle_cfg(ws[r])
+            fo, log = ora.run(cfg, f0[r].copy(), 32)
+            e = rel_err(b.run(r).get_state(), fo, cfg.solid_mask())
+            print("c5 run %d (%d x %d): max |df| / max |f| %.3g, Ehrenfests' sites %d"
+                  % (r, ws[r].nx, ws[r].ny, e, log.counts.sum()))
+            assert e < 1e-5
+            assert np.array_equal(b.run(r).counts(32), log.counts)
+    finally:
+        b.close()
