@@ -66,6 +66,10 @@ def test_host_argument_checks_need_no_gpu(lib):
     assert lib.lb_create(1, 64, 32, 0, 0.1, 1e-3, 4, C.byref(b), lbm.LB_F32, None, C.byref(h)) == lbm.LB_ERR_ARG
     b = lbm.boundaries((lbm.LB_PERIODIC, lbm.LB_BB, lbm.LB_BB, lbm.LB_BB))
     assert lib.lb_create(1, 64, 32, 0, 0.1, 1e-3, 4, C.byref(b), lbm.LB_F32, None, C.byref(h)) == lbm.LB_ERR_ARG
+    b = lbm.boundaries(obstacle=(20, 10, 4, 4), wall=7)                # unknown wall rule
+    assert lib.lb_create(1, 64, 32, 0, 0.1, 1e-3, 4, C.byref(b), lbm.LB_F32, None, C.byref(h)) == lbm.LB_ERR_ARG
+    # a population array of 2^31 values or more
+    assert lib.lb_create(1, 65536, 4096, 0, 0.1, 1e-3, 4, None, lbm.LB_F32, None, C.byref(h)) == lbm.LB_ERR_ARG
     assert lib.lb_step(None, 1) == lbm.LB_ERR_ARG
     lib.lb_destroy(None)   # NULL-safe
     assert lib.lb_mlp_param_count() == 64 * 4 + 64 + 64 * 64 + 64 + 4 * 64 + 4 + 12

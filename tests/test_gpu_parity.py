@@ -312,3 +312,35 @@ def test_storage_error_vs_fp64_gpu_run(lbm, prec):
     tol_u = {"f32": 1.8e-3, "f32dev": 1.1e-4, "f16dev": 5e-2}[prec]
     assert e_M < tol_m and e_rho < tol_m, (e_M, e_rho)
     assert e_u < tol_u, e_u
+
+
+@pytest.mark.parametrize("case", ["tiny_periodic", "k_above_sites", "negative_delta", "k_zero"])
+def test_degenerate_cases_match_the_oracle(lbm, case):
+    # a grid far narrower than one tile (5 x 12: one ragged tile column, a
+    # full and a ragged tile row), more Ehrenfests' sites allowed than there
+    # are sites, a threshold every site passes (dS >= 0 > delta), and no
+    # regulariser
+    if case == "tiny_periodic":
+        w = inputs.Workload("tiny", inputs.D2Q9, 5, 12, inputs.EQ_POLY, 1e-3, 1e-9, 2, 5,
+                            (inputs.BC_PERIODIC,) * 4)
+    else:
+        w = WORKLOADS["closed_box"]()
+        w.k = {"k_above_sites": 10 * w.n_sites, "negative_delta": 7, "k_zero": 0}[case]
+        if case == "negative_delta":
+            w.delta = -1.0
+    cfg = oracle_cfg(w)
+    f0 = perturbed_state(cfg, w, seed=13, eps=0.05)
+    g = gpu_run(lbm, w, "f64")
+    g.set_state(f0)
+    fo, log = ora.run(cfg, f0.copy(), 4)
+    g.step(4)
+    g.sync()
+    assert rel_err(g.get_state(), fo) < 1e-13
+    assert list(g.counts(4)) == list(log.counts)
+    fluid = int((~cfg.solid_mask()).sum())
+    if case == "k_above_sites":
+        assert log.counts.max() <= fluid
+    if case == "negative_delta":
+        assert (log.counts == 7).all()        # every fluid site qualifies; k of them taken
+    if case == "k_zero":
+        assert (log.counts == 0).all()
