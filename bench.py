@@ -15,7 +15,6 @@ Ehrenfests' step (one single-block kernel).
 import argparse
 import hashlib
 import json
-import math
 import os
 import subprocess
 import sys

@@ -5,7 +5,6 @@ The GPU eliminates the density multiplier by normalisation and solves for
 the other three (FP32 iterations, FP64 final steps); the root is unique, so
 the quasiequilibrium must agree with the oracle's to the Newton tolerance.
 """
-import math
 
 import numpy as np
 import pytest

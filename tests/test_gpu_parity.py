@@ -6,7 +6,6 @@ Tolerances:
   selection), 1e-13 on one step.
   FP32 storage: 1e-5 relative on moments after 1000 steps.
 """
-import math
 
 import numpy as np
 import pytest

@@ -8,7 +8,6 @@ selection of the allocating entry point lb_select_only on the same values.
 This file is collected last so that a run stopping at the first failure has
 already run every other test.
 """
-import ctypes as C
 
 import numpy as np
 import pytest
