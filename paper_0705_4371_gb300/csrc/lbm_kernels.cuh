@@ -203,14 +203,16 @@ __device__ __noinline__ double delta_s_fp64(PopArr<L::Q, T> g, double rho0) {
 // slowest lane holds its whole warp).  a = 2 when f = f*; alpha_max when
 // the entropy still exceeds S(f) there; -1 when some f_i or f*_i is not
 // positive.
-// FP32 near equilibrium (max |x| < 0.1, almost every site) takes a branch-
-// free path instead: with Sn = sum f_i x_i^n, the series of G / a is
+// Near equilibrium (max |x| < 0.1, almost every site) both precisions take
+// a branch-free path instead: with Sn = sum f_i x_i^n, the series of G / a is
 //   P(a) = sum_{n>=2} (-1)^n Sn (a^{n-1}/n - 1)/(n - 1),
 // whose terms beyond n = 10 are below 1e-9 S2 for |a x| <= 0.21 (the root
 // lies within 2 +- max|x| / 3 there), far below FP32's rounding of P (about
-// 1e-7 S2); three Newton steps on P from the series root 2 + S3 / (3 S2)
-// reach the FP32 root (P is almost linear: P' ~ S2 / 2).  No logarithm and
-// no data-dependent loop, so the lanes of a warp stay together.
+// 1e-7 S2), and beyond n = 24 below 1e-18 S2, under FP64's; Newton steps on
+// P from the series root 2 + S3 / (3 S2) (three in FP32, four in FP64: P is
+// almost linear, P' ~ S2 / 2, and the start is off by O(max|x|^2)) reach the
+// root.  No logarithm and no data-dependent loop, so the lanes of a warp stay
+// together.
 template <int Q, int NT, typename U>
 __device__ __forceinline__ U elbm_alpha_series(const U* D, const U* x) {
     // c_n = (-1)^n Sn / (n - 1), n = 2..NT, with Sn = sum D_i x_i^{n-1}
@@ -240,7 +242,7 @@ __device__ __forceinline__ U elbm_alpha_series(const U* D, const U* x) {
     }
     U a = a0;
 #pragma unroll
-    for (int it = 0; it < 3; it++) {
+    for (int it = 0; it < (sizeof(U) == 8 ? 4 : 3); it++) {
         U B = b[NT], dP = d[NT];
 #pragma unroll
         for (int n = NT - 1; n >= 2; n--) {
@@ -271,9 +273,9 @@ __device__ __noinline__ U elbm_alpha(const U* f, const U* fs) {
     }
     if (!positive) return U(-1);
     if (!moved || !(xneg > U(0))) return U(2);
-    if constexpr (!fp64) {
-        if (xm < U(0.1)) return elbm_alpha_series<L::Q, 10, U>(D, x);
-    }
+    // near equilibrium the series path: terms to n = 10 reach FP32's rounding,
+    // to n = 24 FP64's (the omitted terms are below 1e-18 S2 for |a x| <= 0.21)
+    if (xm < U(0.1)) return elbm_alpha_series<L::Q, fp64 ? 24 : 10, U>(D, x);
 #pragma unroll
     for (int i = 0; i < L::Q; i++) {
         R += D[i] * log1p(x[i]);
