@@ -222,6 +222,8 @@ def main(argv=None):
     c.add_argument("--wall", choices=["bounce-back", "diffuse"], default="bounce-back")
     c.add_argument("--steps", type=int, default=None)
     c.add_argument("--collision", choices=["lbgk", "elbm"], default="lbgk")
+    sh = sub.add_parser("shock")
+    sh.add_argument("--steps", type=int, default=400)
     b = sub.add_parser("batch")
     b.add_argument("--runs", type=int, default=24)
     b.add_argument("--steps", type=int, default=44)
@@ -232,6 +234,12 @@ def main(argv=None):
         energy_case(a.eq, a.steps, a.nx, a.ny)
     elif a.case == "elbm":
         elbm_case(a.steps, a.nx, a.ny)
+    elif a.case == "shock":
+        # the nine panels of the Sec. 4.1 figure: excess total variation of rho
+        # and Ehrenfests' sites over the run
+        for name in sorted(SHOCK_PANELS):
+            r, _, counts = shock_panel(name, a.steps)
+            print("panel %s: excess TV of rho %.4f, Ehrenfests' sites %d" % (name, oscillation(r), int(counts.sum())))
     elif a.case == "cylinder":
         import json
         wall = inputs.WALL_DIFFUSE if a.wall == "diffuse" else inputs.WALL_BOUNCE_BACK
