@@ -13,7 +13,7 @@ import pytest
 
 from oracle import core as ora
 from paper_0705_4371_gb300 import inputs
-from tests._common import oracle_cfg, rel_err
+from tests._common import moment_errors, oracle_cfg, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -165,3 +165,54 @@ def test_full_size_c5_batch_runs_match_the_oracle(lbm, variant):
             assert np.array_equal(b.run(r).counts(32), log.counts)
     finally:
         b.close()
+
+
+def test_full_size_precision_form_error_table(lbm):
+    # the precision form at its own size: the 4096 x 2048 cylinder at Re 20000
+    # for 1000 steps from the seeded inflow (noise 1e-4); every storage replays
+    # the FP64 GPU run's selections; moment errors against that run.  The
+    # unstable shear layers of Re 20000 amplify rounding over the run, so
+    # the bounds here are looser than the Re 1000 ones of the small grid.
+    w = inputs.workload_c3()
+    rho, ux, uy = inputs.cylinder_fields(w)
+    ref = lbm.Lattice.from_workload(w, precision=lbm.LB_F64)
+    ref.init_equilibrium(rho, ux, uy)
+    sels = []
+    for _ in range(1000):
+        ref.step(1)
+        sels.append(ref.selected())
+    r64, u64, v64, _ = ref.moments()
+    ref.close()
+    m = w.solid_mask()
+    out = {}
+    for prec in ("f32", "f32dev", "f16dev"):
+        with lbm.Lattice.from_workload(w, precision=lbm.PRECISIONS[prec]) as g:
+            g.init_equilibrium(rho, ux, uy)
+            g.replay_selection(sels)
+            g.step(1000)
+            r, u, v, _ = g.moments()
+        out[prec] = moment_errors((r, u, v), (r64, u64, v64), m, w.u_in[0])
+        print("4096 x 2048, 1000 steps, %s vs FP64 GPU: M %.3g rho %.3g u %.3g" % ((prec,) + out[prec]))
+    assert sum(len(s) for s in sels) > 0
+    assert out["f32dev"][0] < 1e-4 and out["f32"][0] < 1e-3 and out["f16dev"][0] < 3e-2
+    assert out["f32dev"][0] <= out["f32"][0]     # deviation storage is the more accurate
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32dev", 1e-4), ("f32", 1e-3), ("f16dev", 3e-2)])
+def test_scaled_precision_workload_vs_the_oracle(lbm, prec, tol):
+    # the same layout at 1/8 scale (512 x 256, L = 16, Re 20000) against the
+    # FP64 oracle, 1000 steps with the oracle's selections replayed
+    w = inputs.workload_c3_scaled()
+    cfg = oracle_cfg(w)
+    rho, ux, uy = inputs.cylinder_fields(w)
+    fo, log = ora.run(cfg, ora.init_field(cfg, rho, ux, uy), 1000)
+    ro, uo, vo, _ = ora.moment_fields(cfg, fo)
+    with lbm.Lattice.from_workload(w, precision=lbm.PRECISIONS[prec]) as g:
+        g.init_equilibrium(rho, ux, uy)
+        g.replay_selection(log.selected)
+        g.step(1000)
+        r, u, v, _ = g.moments()
+    e = moment_errors((r, u, v), (ro, uo, vo), cfg.solid_mask(), w.u_in[0])
+    print("512 x 256, 1000 steps, %s vs oracle: M %.3g rho %.3g u %.3g (Ehrenfests' sites %d)"
+          % ((prec,) + e + (int(log.counts.sum()),)))
+    assert e[0] < tol and e[1] < tol
