@@ -114,6 +114,7 @@ def load(path=None):
 
 
 def last_error():
+    """Message of the calling thread's last failed library call (lb_last_error)."""
     return load().lb_last_error().decode()
 
 
@@ -136,6 +137,8 @@ def _f64(a):
 
 
 def boundaries(kinds=(LB_BB,) * 4, rho_in=1.0, u_in=(0.0, 0.0), obstacle=(0, 0, 0, 0), wall=0):
+    """An lb_boundaries struct: side kinds (x0, x1, y0, y1), inlet state, obstacle rectangle (x0,
+    y0, w, h; w = 0: none) and its wall rule."""
     b = lb_boundaries()
     b.kind_x0, b.kind_x1, b.kind_y0, b.kind_y1 = kinds
     b.rho_in = rho_in
@@ -168,6 +171,7 @@ def select_only_noalloc(ds_ptr, n, delta, k, idx_ptr, count_ptr, stream=None):
 
 
 def mlp_param_count():
+    """Number of FP32 parameters of the 4-64-64-4 network (lb_mlp_param_count)."""
     return load().lb_mlp_param_count()
 
 
@@ -187,28 +191,34 @@ def mlp_init(seed):
 
 
 def energy_dataset(rho, ux, uy, escale, n, feat, dmu, mu=None, stats=None, stream=None):
+    """lb_energy_dataset: features and multiplier targets of n samples by the GPU Newton solve."""
     _check(load().lb_energy_dataset(_vp(rho), _vp(ux), _vp(uy), _vp(escale), int(n), _vp(feat),
                                     _vp(dmu), _vp(mu), _vp(stats), _vp(stream)))
 
 
 def mlp_normalise(params, feat, dmu, n, stream=None):
+    """lb_mlp_normalise: fold the training set's standardisation into the parameters."""
     _check(load().lb_mlp_normalise(_vp(params), _vp(feat), _vp(dmu), int(n), _vp(stream)))
 
 
 def mlp_forward(params, feat, n, y, stream=None):
+    """lb_mlp_forward: network outputs y[n][4] for features feat[n][4]."""
     _check(load().lb_mlp_forward(_vp(params), _vp(feat), int(n), _vp(y), _vp(stream)))
 
 
 def mlp_grad(params, feat, dmu, n, grad, loss=None, stream=None):
+    """lb_mlp_grad: gradient (and optionally the loss) of the mean squared error."""
     _check(load().lb_mlp_grad(_vp(params), _vp(feat), _vp(dmu), int(n), _vp(grad), _vp(loss),
                               _vp(stream)))
 
 
 def mlp_adam(params, grad, m, v, t, lr, stream=None):
+    """lb_mlp_adam: one Adam update of the parameters."""
     _check(load().lb_mlp_adam(_vp(params), _vp(grad), _vp(m), _vp(v), int(t), float(lr), _vp(stream)))
 
 
 def mlp_train(params, feat, dmu, n, batch, epochs, lr0, lr1, loss_log=None, stream=None):
+    """lb_mlp_train: epochs of mini-batch Adam with a geometric learning-rate decay."""
     _check(load().lb_mlp_train(_vp(params), _vp(feat), _vp(dmu), int(n), int(batch), int(epochs),
                                float(lr0), float(lr1), _vp(loss_log), _vp(stream)))
 
@@ -249,6 +259,7 @@ class Lattice:
                    stream)
 
     def close(self):
+        """Destroy the run (lb_destroy); a run borrowed from a batch is left to the batch."""
         if getattr(self, "h", None):
             if not getattr(self, "_borrowed", False):
                 self.L.lb_destroy(self.h)
@@ -268,85 +279,113 @@ class Lattice:
 
     @property
     def shape(self):
+        """(ny, nx) of the site fields."""
         return (self.ny, self.nx)
 
     def init_equilibrium(self, rho, ux, uy=None, e2=None):
+        """Quasiequilibrium of the given host fields at every fluid site (lb_init_equilibrium); e2
+        (2E) for the energy forms."""
         rho, ux, uy, e2 = _f64(rho), _f64(ux), _f64(uy), _f64(e2)
         _check(self.L.lb_init_equilibrium(self.h, _ptr(rho), _ptr(ux), _ptr(uy), _ptr(e2)))
 
     def get_state(self):
+        """Pre-collision populations of the current step, FP64 [Q][ny][nx] in the paper's numbering
+        (lb_get_state)."""
         f = np.zeros((self.q, self.ny, self.nx))
         _check(self.L.lb_get_state(self.h, _ptr(f)))
         return f
 
     def set_state(self, f):
+        """Load populations (FP64 [Q][ny][nx]); the next step starts from them (lb_set_state)."""
         f = _f64(f)
         assert f.size == self.q * self.nx * self.ny
         _check(self.L.lb_set_state(self.h, _ptr(f)))
 
     def step(self, n=1):
+        """Queue n time steps on the run's stream (lb_step; graphs of 32 steps where possible);
+        raises on a sticky error of earlier work."""
         return _check(self.L.lb_step(self.h, int(n)))
 
     def sync(self):
+        """Wait for the run's queued work (lb_sync)."""
         return _check(self.L.lb_sync(self.h))
 
     def moments(self):
+        """(rho, ux, uy, 2E) of the current pre-collision state as FP64 host arrays [ny][nx]
+        (lb_moments)."""
         rho, ux, uy, e2 = (np.zeros(self.shape) for _ in range(4))
         _check(self.L.lb_moments(self.h, _ptr(rho), _ptr(ux), _ptr(uy), _ptr(e2), 0))
         return rho, ux, uy, e2
 
     def moments_device(self, rho_ptr, ux_ptr, uy_ptr=None, e2_ptr=None):
+        """lb_moments into caller-provided device arrays (integer pointers; asynchronous)."""
         _check(self.L.lb_moments(self.h, _ptr(rho_ptr), _ptr(ux_ptr), _ptr(uy_ptr), _ptr(e2_ptr), 1))
 
     def delta_s(self):
+        """Exact dS of every site of the current pre-collision state (NaN at solid sites;
+        lb_delta_s)."""
         ds = np.zeros(self.shape)
         _check(self.L.lb_delta_s(self.h, _ptr(ds), 0))
         return ds
 
     def selected(self, cap=1 << 20):
+        """Sorted indices y nx + x of the sites the last step moved to f* (lb_selected)."""
         idx = np.zeros(cap, np.int32)
         cnt = C.c_int(0)
         _check(self.L.lb_selected(self.h, _ptr(idx), cap, C.byref(cnt)))
         return np.sort(idx[:min(cnt.value, cap)].astype(np.int64))
 
     def counts(self, n):
+        """Ehrenfests' sites of each of the last n steps, oldest first (lb_counts)."""
         out = np.zeros(n, np.int32)
         _check(self.L.lb_counts(self.h, _ptr(out), int(n)))
         return out
 
     def set_probe(self, x, y):
+        """Log u_x at site (x, y) every step (lb_set_probe)."""
         _check(self.L.lb_set_probe(self.h, int(x), int(y)))
 
     def probe(self, n):
+        """The last n logged u_x values of the probe site, oldest first (lb_probe)."""
         out = np.zeros(n)
         _check(self.L.lb_probe(self.h, _ptr(out), int(n)))
         return out
 
     def set_log_capacity(self, n):
+        """Steps kept by the count and probe rings (lb_set_log_capacity)."""
         _check(self.L.lb_set_log_capacity(self.h, int(n)))
 
     def replay_selection(self, selections):
+        """Make the next len(selections) steps take the given sets as their Ehrenfests' sites
+        (lb_replay_selection)."""
         counts = np.array([len(s) for s in selections], np.int32)
         idx = np.concatenate([np.asarray(s, np.int32) for s in selections] + [np.zeros(0, np.int32)])
         idx = np.ascontiguousarray(idx, np.int32)
         _check(self.L.lb_replay_selection(self.h, _ptr(counts), _ptr(idx), len(selections)))
 
     def set_collision(self, collision):
+        """LB_COLLISION_LBGK or LB_COLLISION_ELBM (entropic f* only; lb_set_collision)."""
         _check(self.L.lb_set_collision(self.h, int(collision)))
 
     def set_mlp(self, params):
+        """Load the learned form's network (host FP32 parameters; lb_set_mlp)."""
         p = np.ascontiguousarray(params, np.float32)
         _check(self.L.lb_set_mlp(self.h, _ptr(p), p.size))
 
     def newton_stats(self, reset=False):
+        """(FP32 iterations, finishing iterations, sites solved, sites that missed 1e-12) of the
+        energy forms (lb_newton_stats)."""
         v = [C.c_longlong(0) for _ in range(4)]
         _check(self.L.lb_newton_stats(self.h, *(C.byref(x) for x in v), int(reset)))
         return tuple(x.value for x in v)
 
     def set_timing(self, enable):
+        """Time every stream-collide launch with CUDA events (direct launches instead of graphs;
+        lb_set_timing)."""
         _check(self.L.lb_set_timing(self.h, int(bool(enable))))
 
     def kernel_times(self, reset=False):
+        """Summed kernel milliseconds and launch counts since the last reset (lb_kernel_times)."""
         cm, sm = C.c_double(0), C.c_double(0)
         cn, sn = C.c_longlong(0), C.c_longlong(0)
         _check(self.L.lb_kernel_times(self.h, C.byref(cm), C.byref(cn), C.byref(sm), C.byref(sn),
@@ -355,9 +394,13 @@ class Lattice:
                 "select_ms": sm.value, "select_launches": sn.value}
 
     def set_tile_shape(self, shape):
+        """Tile shape of the D2Q9 stream-collide kernel (0-6; lb_set_tile_shape); results do not
+        depend on it."""
         _check(self.L.lb_set_tile_shape(self.h, int(shape)))
 
     def info(self):
+        """Run facts: populations, row padding, bytes per population and per site update, launches
+        per step, grid, tile shape, beta (lb_info)."""
         out = np.zeros(8, np.int64)
         beta = C.c_double(0)
         _check(self.L.lb_info(self.h, _ptr(out), C.byref(beta)))
@@ -389,38 +432,52 @@ class Batch:
                       for r, w in enumerate(workloads)]
 
     def run(self, r):
+        """The r-th run as a Lattice (borrowed: its state, logs and exports; stepping goes through
+        the batch)."""
         return self._runs[r]
 
     def __len__(self):
         return len(self._runs)
 
     def step(self, n=1):
+        """Advance every run by n steps with the chosen launch strategy (lb_batch_step)."""
         _check(self.L.lb_batch_step(self.h, int(n)))
 
     def step_sequential(self, n=1):
+        """Advance every run by n steps, one run after another through its own graphs
+        (lb_batch_step_sequential)."""
         _check(self.L.lb_batch_step_sequential(self.h, int(n)))
 
     def sync(self):
+        """Wait for the batch's queued work (lb_batch_sync)."""
         _check(self.L.lb_batch_sync(self.h))
 
     def set_variant(self, v):
+        """Launch strategy: 0/1 batched kernel with 8- or 4-row tiles, 2 concurrent per-run kernels
+        (lb_batch_set_variant)."""
         _check(self.L.lb_batch_set_variant(self.h, int(v)))
 
     def autotune(self, steps=20, cache_path=None):
+        """Time every strategy (or read the cache) and keep the fastest; returns its number
+        (lb_batch_autotune)."""
         v = C.c_int(-1)
         _check(self.L.lb_batch_autotune(self.h, int(steps), cache_path.encode() if cache_path else None,
                                         C.byref(v)))
         return v.value
 
     def set_timing(self, enable):
+        """Time each step of the batch with CUDA events (lb_batch_set_timing)."""
         _check(self.L.lb_batch_set_timing(self.h, int(enable)))
 
     def kernel_times(self, reset=False):
+        """Summed step milliseconds and step counts since the last reset (lb_batch_kernel_times)."""
         ms, n = C.c_double(0), C.c_longlong(0)
         _check(self.L.lb_batch_kernel_times(self.h, C.byref(ms), C.byref(n), int(reset)))
         return {"ms": ms.value, "launches": n.value}
 
     def info(self):
+        """Batch facts: runs, sites, tiles, grid, blocks per SM, strategy, tile rows, graph steps
+        (lb_batch_info)."""
         out = np.zeros(8, np.int64)
         _check(self.L.lb_batch_info(self.h, _ptr(out)))
         keys = ("runs", "sites", "tiles", "grid_blocks", "blocks_per_sm", "variant", "tile_rows",
@@ -428,6 +485,7 @@ class Batch:
         return dict(zip(keys, (int(x) for x in out)))
 
     def close(self):
+        """Destroy the batch and its runs (lb_batch_destroy)."""
         if getattr(self, "h", None):
             for r in self._runs:
                 r.h = None
