@@ -15,6 +15,9 @@ D1Q3, D2Q9 = 0, 1
 EQ_POLY, EQ_ENTROPIC, EQ_ENERGY = 0, 1, 2
 BC_BB, BC_FREESLIP, BC_INLET, BC_OUTLET, BC_PERIODIC = 0, 1, 2, 3, 4
 WALL_BOUNCE_BACK, WALL_DIFFUSE = 0, 1
+# storage of the populations (precision form): FP64, FP32, FP32 and FP16
+# deviations f - W rho0 (rho0 = 1)
+STORE_F64, STORE_F32, STORE_F32_DEV, STORE_F16_DEV = 0, 1, 2, 3
 
 _lib = None
 
@@ -25,7 +28,7 @@ class _Cfg(C.Structure):
                 ("k", C.c_long), ("bc", C.c_int * 4), ("rho_in", C.c_double),
                 ("ux_in", C.c_double), ("uy_in", C.c_double), ("ox0", C.c_int),
                 ("oy0", C.c_int), ("ow", C.c_int), ("oh", C.c_int), ("elbm", C.c_int),
-                ("wall", C.c_int)]
+                ("wall", C.c_int), ("store", C.c_int)]
 
 
 def lib():
@@ -61,6 +64,10 @@ def lib():
                               C.c_void_p, C.c_long, C.c_void_p, C.c_int, C.c_int]
         L.ora_collide.argtypes = [cfgp, dp, C.c_void_p, C.c_long, dp]
         L.ora_stream.argtypes = [cfgp, dp, dp]
+        L.ora_round_f32.argtypes = [C.c_double]
+        L.ora_round_f32.restype = C.c_double
+        L.ora_round_f16.argtypes = [C.c_double]
+        L.ora_round_f16.restype = C.c_double
         L.ora_num_threads.restype = C.c_int
         L.ora_set_num_threads.argtypes = [C.c_int]
         _lib = L
@@ -103,6 +110,7 @@ class Config:
     obstacle: tuple = (0, 0, 0, 0)
     elbm: bool = False        # collision (elbmLB) instead of (lbgkLB)
     wall: int = 0             # rule on the obstacle's faces: WALL_BOUNCE_BACK / WALL_DIFFUSE
+    store: int = 0            # storage of the populations: STORE_F64 / _F32 / _F32_DEV / _F16_DEV
 
     @property
     def q(self):
@@ -122,6 +130,7 @@ class Config:
         s.ox0, s.oy0, s.ow, s.oh = self.obstacle
         s.elbm = 1 if self.elbm else 0
         s.wall = self.wall
+        s.store = self.store
         return s
 
     def solid_mask(self):
@@ -296,6 +305,16 @@ def stream(cfg, fp):
     s = cfg.c_struct()
     lib().ora_stream(C.byref(s), np.ascontiguousarray(fp), f)
     return f
+
+
+def round_f32(x):
+    """x rounded to the nearest IEEE binary32 value (ties to even)."""
+    return lib().ora_round_f32(float(x))
+
+
+def round_f16(x):
+    """x rounded to the nearest IEEE binary16 value (ties to even)."""
+    return lib().ora_round_f16(float(x))
 
 
 def num_threads():

@@ -24,6 +24,9 @@
  *      take the LBGK step f + 2 beta (f* - f)                        (ESLB);
  *   4. free flight: f(x, t+1) = f'(x - v_i, t) with the boundary rules of
  *      Sec. 4.2 (exact shift on the grid, Sec. 3.2 last paragraph).
+ * With a storage type other than FP64 (the precision form), the
+ * post-collision populations of step 3 are rounded to that type before the
+ * free flight, as a field stored in that type holds them.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -504,7 +507,58 @@ typedef struct {
     int ox0, oy0, ow, oh;          /* solid rectangle; ow == 0: none */
     int elbm;                      /* collision (elbmLB) instead of (lbgkLB) */
     int wall;                      /* rule on the rectangle's faces: ORA_WALL_* */
+    int store;                     /* storage of the populations: ORA_STORE_* */
 } ora_cfg;
+
+/* ------------------------------------------------------------------ */
+/* Storage of the populations (the precision form: populations stored  */
+/* in FP32 or FP16, as f or as deviations f - W_i rho0 with rho0 = 1).  */
+/* The method computes in exact (here FP64) arithmetic; what a stored   */
+/* field can hold is the value rounded to the storage type, once per    */
+/* time step, when the post-collision populations are written.          */
+/* ------------------------------------------------------------------ */
+enum { ORA_STORE_F64 = 0, ORA_STORE_F32 = 1, ORA_STORE_F32_DEV = 2, ORA_STORE_F16_DEV = 3 };
+
+/* Round to nearest, ties to even, to a binary floating-point format with
+ * p significand bits and smallest normal exponent emin (IEEE 754 binary32:
+ * p = 24, emin = -126; binary16: p = 11, emin = -14), overflow to +-inf at
+ * max_finite.  Written from the format's definition: below 2^emin the
+ * spacing is the subnormal quantum 2^(emin - p + 1); above it, the spacing
+ * is 2^(e - p + 1) for x in [2^e, 2^(e+1)).  nearbyint rounds ties to even
+ * in the default rounding mode. */
+static double round_to_format(double x, int p, int emin, double max_finite)
+{
+    if (!isfinite(x) || x == 0.0) return x;
+    int e;
+    frexp(x, &e);             /* |x| in [2^(e-1), 2^e) */
+    e -= 1;
+    if (e < emin) e = emin;
+    double q = ldexp(1.0, e - p + 1);
+    double r = nearbyint(x / q) * q;   /* x / q and r * q are exact scalings */
+    if (fabs(r) > max_finite) {
+        /* beyond the largest finite value: rounds to infinity at and above
+         * max_finite + half its spacing */
+        double half = ldexp(1.0, (int)(log2(max_finite)) - p);
+        if (fabs(x) >= max_finite + half) return x > 0 ? INFINITY : -INFINITY;
+        return x > 0 ? max_finite : -max_finite;
+    }
+    return r;
+}
+
+double ora_round_f32(double x) { return round_to_format(x, 24, -126, 3.4028234663852886e38); }
+double ora_round_f16(double x) { return round_to_format(x, 11, -14, 65504.0); }
+
+/* Value of one stored population of weight w (rho0 = 1 for the deviation
+ * forms). */
+static double stored_value(int store, double f, double w)
+{
+    switch (store) {
+        case ORA_STORE_F32: return ora_round_f32(f);
+        case ORA_STORE_F32_DEV: return w + ora_round_f32(f - w);
+        case ORA_STORE_F16_DEV: return w + ora_round_f16(f - w);
+        default: return f;
+    }
+}
 
 static int is_solid(const ora_cfg* c, int x, int y)
 {
@@ -761,6 +815,8 @@ int ora_run(const ora_cfg* c, double* f, long nsteps,
                 if (!elig[s]) fp[i * N + s] = 0.0;
                 else if (chosen[s]) fp[i * N + s] = fsi;
                 else fp[i * N + s] = fi + a * c->beta * (fsi - fi);
+                if (c->store != ORA_STORE_F64 && elig[s])
+                    fp[i * N + s] = stored_value(c->store, fp[i * N + s], lat_w(L, i));
             }
         }
         /* 4. free flight with boundary rules */
