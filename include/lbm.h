@@ -200,14 +200,15 @@ int lb_select_only(const double* ds, int n, double delta, int k, int* idx_out, i
 #define LB_NOALLOC_MAX_N 262144
 
 /* lb_select_only_noalloc -- the paper has no counterpart to this entry point;
- * it exists for callers that cannot allocate device memory (code running
- * while a stream is captured, real-time loops that must not take
- * cudaMalloc's implicit device synchronisation, hosts that manage all device
- * memory themselves).  It makes the same selection as lb_select_only: among
+ * it exists for callers that cannot allocate device memory: hosts whose own
+ * allocator has reserved the device memory and hands it out itself, and
+ * real-time loops that must not take cudaMalloc's implicit device
+ * synchronisation or its latency.  It makes the same selection as lb_select_only: among
  * ds[0..n) the k largest values > delta (all of them if fewer qualify), ties
  * to the lower index, through the same kernels.
- *   ds:      DEVICE pointer to n FP64 values (read);
- *   idx_out: DEVICE pointer to min(n, k) ints (written; order unspecified);
+ *   ds:      DEVICE pointer to n FP64 values (read; may be NULL when n = 0);
+ *   idx_out: DEVICE pointer to min(n, k) ints (written; order unspecified;
+ *            may be NULL when n = 0 or k = 0);
  *   count:   DEVICE pointer to one int (written: the number selected);
  *   cuda_stream: the stream the work is queued on (NULL: the legacy default
  *            stream).  The call is asynchronous: the outputs are valid once

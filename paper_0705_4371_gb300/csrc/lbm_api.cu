@@ -42,7 +42,6 @@ int fail(int code, const char* fmt, ...) {
                         "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
     } while (0)
 
-constexpr int kStageCap = 8192;      // candidates staged in shared memory by the select kernel
 constexpr int kGraphSteps = 32;      // steps per captured graph (even: buffers return)
 constexpr int kDefaultLog = 65536;
 constexpr int kDefaultTileShape = 4;  // fastest measured on GB300 (staged tiles, 2 in flight)
@@ -497,7 +496,7 @@ int lb_create(int lattice, int nx, int ny, int equilibrium, double nu, double de
     CKH(cudaMemsetAsync(h->d_step, 0, sizeof(long long), h->stream));
     CKH(cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), h->stream));
     CKH(cudaMemsetAsync(h->newton_stats, 0, 4 * sizeof(unsigned long long), h->stream));
-    CKH(h->L.set_smem(kStageCap));
+    CKH(h->L.set_smem(kSelectStageCap));
     if (size_grid(h) != LB_OK || make_tensor_maps(h) != LB_OK) {
         const std::string msg = g_last_error;
         lb_destroy(h);
@@ -779,9 +778,9 @@ int lb_select_only(const double* ds, int n, double delta, int k, int* idx_out, i
         P.cand_key = key; P.cand_idx = cid; P.cand_count = ccount; P.cand_per_block = per_block;
         P.sel_idx = sel; P.sel_count = scount; P.step = step; P.err = err; P.ring_cap = 1;
         Launchers L = launchers_f64(LB_D1Q3, LB_EQ_POLY);
-        ok(L.set_smem(kStageCap));
+        ok(L.set_smem(kSelectStageCap));
         ok(launch_emit_from_ds(P, d_ds, n, st));
-        ok(L.select(P, kStageCap, 1, st));
+        ok(L.select(P, kSelectStageCap, 1, st));
         int c = 0;
         ok(cudaMemcpyAsync(&c, scount, sizeof(int), cudaMemcpyDeviceToHost, st));
         ok(cudaStreamSynchronize(st));

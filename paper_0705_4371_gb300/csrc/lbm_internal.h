@@ -34,6 +34,10 @@ Launchers launchers_f16_energy(int eq);
 
 constexpr int kTileShapes = 7;   // tile shapes of the D2Q9 stream-collide kernel
 
+// Candidates the stand-alone select kernel stages in shared memory (its
+// dynamic shared-memory limit is set from this one value by every caller).
+constexpr int kSelectStageCap = 8192;
+
 // Rows and columns per block tile of the shared-memory-staged shapes
 // (rows 0: not staged).
 inline int staged_rows(int tile_shape) {

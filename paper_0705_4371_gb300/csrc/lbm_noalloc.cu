@@ -1,9 +1,9 @@
 // lbm_noalloc.cu -- lb_select_only_noalloc: the selection of the k largest
 // values above a threshold, for callers that cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while a stream is being
-// captured, real-time loops that must not take cudaMalloc's implicit device
-// synchronisation, and hosts that hand out all device memory themselves.
+// Some callers cannot call cudaMalloc: hosts whose own allocator has reserved
+// the device memory and hands it out itself, and real-time loops that must
+// not take cudaMalloc's implicit device synchronisation or its latency.
 // This entry point allocates nothing.  Its working memory is the fixed
 // file-scope device array below; the caller passes the input values and the
 // output index and count buffers, all in device memory.
@@ -21,7 +21,6 @@ using namespace lbm;
 
 namespace {
 
-constexpr int kStageCap = 8192;   // candidates staged in shared memory by the select kernel
 constexpr int kMaxDevices = 64;
 
 // Working memory: candidate keys and site indices (one slot per input value)
@@ -66,7 +65,7 @@ int scratch_for_current_device(NoAllocScratch** out) {
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess)
             return fail(LB_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-        e = launchers_f64(LB_D1Q3, LB_EQ_POLY).set_smem(kStageCap);
+        e = launchers_f64(LB_D1Q3, LB_EQ_POLY).set_smem(kSelectStageCap);
         if (e != cudaSuccess)
             return fail(LB_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
         g_scratch_ptr[dev] = static_cast<NoAllocScratch*>(p);
@@ -79,8 +78,9 @@ int scratch_for_current_device(NoAllocScratch** out) {
 
 extern "C" int lb_select_only_noalloc(const double* ds, int n, double delta, int k, int* idx_out,
                                       int* count, void* cuda_stream) {
-    if (!ds || !idx_out || !count) return fail(LB_ERR_ARG, "NULL device pointer");
     if (n < 0 || k < 0) return fail(LB_ERR_ARG, "n and k must be >= 0");
+    if (!count || (n > 0 && !ds) || (n > 0 && k > 0 && !idx_out))
+        return fail(LB_ERR_ARG, "NULL device pointer");
     if (n > LB_NOALLOC_MAX_N)
         return fail(LB_ERR_ARG, "n = %d exceeds the fixed working memory of %d values", n,
                     LB_NOALLOC_MAX_N);
@@ -108,7 +108,7 @@ extern "C" int lb_select_only_noalloc(const double* ds, int n, double delta, int
     P.sel_idx = idx_out; P.sel_count = count;
     P.step = &s->step; P.err = &s->err; P.ring_cap = 1;
     e = launch_emit_from_ds(P, ds, n, st);
-    if (e == cudaSuccess) e = launchers_f64(LB_D1Q3, LB_EQ_POLY).select(P, kStageCap, 1, st);
+    if (e == cudaSuccess) e = launchers_f64(LB_D1Q3, LB_EQ_POLY).select(P, kSelectStageCap, 1, st);
     if (e != cudaSuccess) return fail(LB_ERR_CUDA, "launch: %s", cudaGetErrorString(e));
     return LB_OK;
 }

@@ -1,9 +1,11 @@
 """lb_select_only_noalloc: the selection entry point for callers that cannot
-allocate device memory (stream capture in progress, real-time loops that must
-not take cudaMalloc's implicit synchronisation, hosts that own all device
-memory).  Its working memory is a fixed array inside the library, so the test
-checks that two calls in a row, which reuse that array, each give exactly the
-selection of the allocating entry point lb_select_only on the same values.
+allocate device memory (hosts whose own allocator has reserved the device
+memory and hands it out itself, real-time loops that must not take
+cudaMalloc's implicit synchronisation).  Its working memory is a fixed array
+inside the library, so the test checks that two calls in a row, which reuse
+that array, each give exactly the oracle's selection (the brute-force rule of
+Sec. 3.2 with ties to the lower index) and the selection of the allocating
+entry point lb_select_only on the same values.
 
 This file is collected last so that a run stopping at the first failure has
 already run every other test.
@@ -12,6 +14,7 @@ already run every other test.
 import numpy as np
 import pytest
 
+from oracle import core as ora
 from paper_0705_4371_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -39,7 +42,7 @@ def _noalloc_select(torch, lbm, ds_host, delta, k):
     return np.sort(out[:c].cpu().numpy().astype(np.int64))
 
 
-def test_two_calls_in_a_row_match_the_allocating_entry_point(env):
+def test_two_calls_in_a_row_match_the_oracle(env):
     torch, lbm = env
     cases = [
         # (seed, n, k, ties, frac_inf, delta quantile)
@@ -50,9 +53,19 @@ def test_two_calls_in_a_row_match_the_allocating_entry_point(env):
         ds = inputs.random_ds_with_ties(seed, n, n_ties=ties, frac_inf=finf)
         delta = float(np.quantile(ds[np.isfinite(ds)], q))
         got = _noalloc_select(torch, lbm, ds, delta, k)
-        ref = lbm.select_only(ds, delta, k)
+        want = ora.select(ds, delta, k)
         assert got.size == min(k, int((ds > delta).sum()))
-        assert np.array_equal(got, ref)
+        assert np.array_equal(got, want)
+        assert np.array_equal(got, lbm.select_only(ds, delta, k))
+
+
+def test_empty_input_selects_nothing(env):
+    torch, lbm = env
+    dev = torch.device("cuda", 0)
+    cnt = torch.full((1,), -1, dtype=torch.int32, device=dev)
+    lbm.select_only_noalloc(0, 0, 0.0, 4, 0, cnt.data_ptr())
+    torch.cuda.synchronize(dev)
+    assert int(cnt.item()) == 0
 
 
 def test_rejects_sizes_beyond_the_fixed_memory(env):
