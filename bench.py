@@ -259,7 +259,7 @@ def run_gpu(args):
     # forms beside the headline (same workload, same timing method)
     forms = {}
     if args.forms and rank == 0:
-        for fname in ("f32dev", "f16dev"):
+        for fname in ("f32", "f32dev", "f16dev"):
             if fname == args.precision:
                 continue
             with lbm.Lattice.from_workload(w, precision=lbm.PRECISIONS[fname],
@@ -581,7 +581,7 @@ def main():
     ap.add_argument("--spinup", type=int, default=200)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c3")
-    ap.add_argument("--precision", default="f32", choices=["f64", "f32", "f32dev", "f16dev"])
+    ap.add_argument("--precision", default="f32dev", choices=["f64", "f32", "f32dev", "f16dev"])
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--tile-shape", type=int, default=-1)
     ap.add_argument("--forms", type=int, default=1)

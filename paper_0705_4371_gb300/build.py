@@ -15,16 +15,19 @@ LIB = os.path.join(HERE, "liblbm.so")
 ROOT = os.path.dirname(HERE)
 HEADERS = [os.path.join(ROOT, "include", "lbm.h")]
 
-SOURCES = ["lbm_kernels_f64.cu", "lbm_kernels_f32.cu", "lbm_kernels_f16.cu",
-           "lbm_energy_f64.cu", "lbm_energy_f32.cu", "lbm_energy_f16.cu",
+SOURCES = ["lbm_kernels_f64.cu", "lbm_kernels_f32.cu", "lbm_kernels_f16.cu", "lbm_kernels_f32p.cu",
+           "lbm_energy_f64.cu", "lbm_energy_f32.cu", "lbm_energy_f16.cu", "lbm_energy_f32p.cu",
            "lbm_api.cu", "lbm_noalloc.cu", "lbm_mlp.cu",
-           "lbm_batch.cu", "lbm_batch_f64.cu", "lbm_batch_f32.cu", "lbm_batch_f16.cu"]
+           "lbm_batch.cu", "lbm_batch_f64.cu", "lbm_batch_f32.cu", "lbm_batch_f16.cu",
+           "lbm_batch_f32p.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-# -fmad=false: no automatic multiply-add contraction; the kernels write their
-# fused multiply-adds explicitly, so every kernel rounds the same way.
+# -fmad=false (device) and -ffp-contract=off (host): no automatic multiply-add
+# contraction; the code writes its fused multiply-adds explicitly, so every
+# kernel, and the host's FP64 boundary values, round the same way on every
+# machine.
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
-         "--expt-relaxed-constexpr", "-fmad=false"]
+         "-Xcompiler", "-ffp-contract=off", "--expt-relaxed-constexpr", "-fmad=false"]
 
 
 def _deps():

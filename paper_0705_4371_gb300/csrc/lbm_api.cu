@@ -59,6 +59,19 @@ int default_tile_shape(int lattice, int eq, int precision) {
 
 size_t storage_bytes(int prec) { return prec == LB_F64 ? 8 : (prec == LB_F16_DEV ? 2 : 4); }
 
+// Half-width of the band around delta in which the precision form decides
+// dS > delta in FP64 rather than in FP32.  The FP32 evaluation of f* leaves
+// an error |e_i| <= ~1e-7 W_i in each nonequilibrium component d_i = f_i - f*_i
+// (a few roundings of quantities below 0.6 W_i); with dS ~ sum d_i^2 / (2 f*_i),
+// its first-order effect on dS is sum |d_i| e_i / f*_i <= 1e-7 sum |d_i| <=
+// 1e-7 sqrt(2 rho dS) ~ 1.5e-7 sqrt(dS) near rho = 1, the second-order one is
+// below 1e-13, and the FP32 sum itself is within ~1e-6 dS.  The band takes
+// twenty times the first-order term, a relative 1e-3 and an absolute 1e-12.
+double recheck_band(double delta) {
+    const double a = std::fabs(delta);
+    return 1e-3 * a + 3e-6 * std::sqrt(a) + 1e-12;
+}
+
 }  // namespace
 
 void lbm::set_last_error(const char* msg) { g_last_error = msg; }
@@ -132,6 +145,26 @@ struct lb_handle {
 
 namespace {
 
+// Inlet populations f*(rho_in, u_in) (Sec. 4.2) in FP64 with the kernels'
+// own formulas, converted as the storage holds them: FP64 f; FP32 and FP16
+// deviation storage the FP32 value of f - W_i (the FP32 arithmetic of both);
+// plain FP32 the FP32 value of f minus the FP32 weight.
+template <typename L>
+void inlet_values_of(const lb_handle* h, double* gin) {
+    double fs[9] = {0};
+    feq_rho_u<L, double>(h->eq, h->bc.rho_in, h->bc.u_in[0], h->bc.u_in[1], 0.0, fs);
+    for (int i = 0; i < 9; i++) gin[i] = 0.0;
+    for (int i = 0; i < L::Q; i++) {
+        if (h->prec == LB_F64) gin[i] = fs[i];
+        else if (h->prec == LB_F32) gin[i] = (double)((float)fs[i] - (float)L::w(i));
+        else gin[i] = (double)(float)(fs[i] - L::w(i));
+    }
+}
+void inlet_values(const lb_handle* h, double* gin) {
+    if (h->lattice == LB_D1Q3) inlet_values_of<D1Q3>(h, gin);
+    else inlet_values_of<D2Q9>(h, gin);
+}
+
 Params make_params(const lb_handle* h, int src, bool prestream) {
     Params P;
     memset(&P, 0, sizeof(P));
@@ -145,6 +178,7 @@ Params make_params(const lb_handle* h, int src, bool prestream) {
     P.bc[0] = h->bc.kind_x0; P.bc[1] = h->bc.kind_x1; P.bc[2] = h->bc.kind_y0; P.bc[3] = h->bc.kind_y1;
     P.rho_in = h->bc.rho_in; P.ux_in = h->bc.u_in[0]; P.uy_in = h->bc.u_in[1];
     P.ox0 = h->bc.obstacle_x0; P.oy0 = h->bc.obstacle_y0; P.ow = h->bc.obstacle_w; P.oh = h->bc.obstacle_h;
+    inlet_values(h, P.gin);
     P.src = h->buf[src];
     P.dst = h->buf[1 - src];
     P.prestream = prestream ? 1 : 0;
@@ -157,6 +191,7 @@ Params make_params(const lb_handle* h, int src, bool prestream) {
     P.replay_cnt = h->replay_cnt; P.replay_off = h->replay_off; P.replay_idx = h->replay_idx;
     P.replay_t0 = h->replay_t0; P.replay_n = h->replay_n;
     P.recheck = (h->prec == LB_F32_DEV || h->prec == LB_F16_DEV) ? 1 : 0;
+    P.recheck_band = recheck_band(h->delta);
     P.mlp = h->mlp; P.newton_stats = h->newton_stats;
     P.ticket = h->ticket;
     P.pend_idx = h->pend_idx;
@@ -246,9 +281,10 @@ int build_graph(lb_handle* h, int start) {
 bool valid_kind(int k) { return k >= LB_BB && k <= LB_OUTLET_COPY; }
 
 // Tensor map describing population buffer b as a 3-D array (x: nx, y: ny,
-// plane: Q) for staged tiles of R = rows rows: box = (128 + 2 H) x (R + 2)
-// x 1 elements, H = 16 bytes of halo on each side and one row above and
-// below; coordinates outside the array read as zero.
+// plane: Q) for staged tiles of R = rows rows: box = (cols + 2 H) x R x 1
+// elements, H = 16 bytes of halo on each side (each plane's copy starts at
+// the row its populations are pulled from); coordinates outside the array
+// read as zero.
 int encode_tensor_map(const lb_handle* h, int b, int rows, int cols, CUtensorMap* out) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
@@ -266,7 +302,7 @@ int encode_tensor_map(const lb_handle* h, int b, int rows, int cols, CUtensorMap
                                                            : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     const cuuint64_t gdim[3] = {(cuuint64_t)h->nx, (cuuint64_t)h->ny, (cuuint64_t)h->Q};
     const cuuint64_t gstride[2] = {(cuuint64_t)h->nxp * es, (cuuint64_t)h->plane * es};
-    const cuuint32_t box[3] = {(cuuint32_t)(cols + 2 * (16 / es)), (cuuint32_t)(rows + 2), 1};
+    const cuuint32_t box[3] = {(cuuint32_t)(cols + 2 * (16 / es)), (cuuint32_t)rows, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = encode(out, dt, 3, h->buf[b], gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -426,7 +462,9 @@ int lb_create(int lattice, int nx, int ny, int equilibrium, double nu, double de
     h->nxp = (nx + 31) / 32 * 32;
     h->eq = equilibrium; h->prec = precision; h->k = k; h->nu = nu; h->delta = delta;
     h->beta = 1.0 / (1.0 + 6.0 * nu);
-    h->rho0 = (precision == LB_F32_DEV || precision == LB_F16_DEV) ? 1.0 : 0.0;
+    // reference density of the deviation arithmetic: every FP32 / FP16 form
+    // (plain FP32 storage keeps f - fl32(W_i)); FP64 works on f itself
+    h->rho0 = precision == LB_F64 ? 0.0 : 1.0;
     h->bc = b;
     h->plane = (long long)ny * h->nxp;
     h->probe_x = h->probe_y = -1;
@@ -435,6 +473,7 @@ int lb_create(int lattice, int nx, int ny, int equilibrium, double nu, double de
     h->replay_t0 = -1;
     if (precision == LB_F64) h->L = launchers_f64(lattice, equilibrium);
     else if (precision == LB_F16_DEV) h->L = launchers_f16(lattice, equilibrium);
+    else if (precision == LB_F32) h->L = launchers_f32p(lattice, equilibrium);
     else h->L = launchers_f32(lattice, equilibrium);
 
 #define CKH(call)                                                                   \

@@ -43,7 +43,9 @@ int fail(int code, const char* fmt, ...) {
                         cudaGetErrorString(e_));                                                  \
     } while (0)
 
-int storage_of(int prec) { return prec == LB_F64 ? 0 : (prec == LB_F16_DEV ? 2 : 1); }
+int storage_of(int prec) {
+    return prec == LB_F64 ? 0 : (prec == LB_F16_DEV ? 2 : (prec == LB_F32 ? 3 : 1));
+}
 
 }  // namespace
 
@@ -571,6 +573,7 @@ namespace lbm {
 BatchLaunchers batch_launchers(int storage, int eq, int variant) {
     if (storage == 0) return batch_launchers_f64(eq, variant);
     if (storage == 2) return batch_launchers_f16(eq, variant);
+    if (storage == 3) return batch_launchers_f32p(eq, variant);
     return batch_launchers_f32(eq, variant);
 }
 

@@ -2,7 +2,8 @@
 // of a batch by one time step.
 //
 // The runs' block tiles (R rows x 128 sites, staged in shared memory by
-// bulk tensor copies exactly as in the single-run staged kernel) form one
+// bulk tensor copies exactly as in the single-run staged kernel: each plane's
+// window is the R rows the tile pulls from it) form one
 // flat list; a persistent grid takes tiles from a global counter, so small
 // and large runs share the GPU without idle tails per run.  A tile's sites
 // go through the same per-site update as a single run (tma_tile), its
@@ -109,7 +110,7 @@ __global__ void __launch_bounds__(32 * R, 16 / R) k_collide_batch(const __grid_c
         S* base = stages + (size_t)st * (LY::STAGE_BYTES / sizeof(S));
 #pragma unroll
         for (int i = 0; i < L::Q; i++)
-            tma_load_3d(base + i * LY::PLANE, A.tm + lo, tx * TX - LY::H, ty * R - 1, i, bar);
+            tma_load_3d(base + i * LY::PLANE, A.tm + lo, tx * TX - LY::H, ty * R - L::cy(i), i, bar);
     };
     if (threadIdx.x == 0)
         for (int st = 0; st < STAGES - 1; st++) fill(st);
@@ -142,7 +143,8 @@ __global__ void __launch_bounds__(32 * R, 16 / R) k_collide_batch(const __grid_c
         const int nf = __syncthreads_or(nonfinite);
         // the tile's pending sites (npend is read between barriers: uniform)
         if (sh.npend > 0) {
-            resolve_list<L, S, EQ>(P, (int)min(sh.npend, (unsigned)kPend), [&](int j) { return sh.pend[j]; });
+            resolve_list<L, S, EQ>(P, (int)min(sh.npend, (unsigned)kPend), [&](int j) { return sh.pend[j]; },
+                                   nullptr, nullptr);
             __syncthreads();
             if (threadIdx.x == 0) sh.npend = 0;
         }

@@ -4,9 +4,10 @@
 // Layout in HBM: populations are SoA planes f[Q][ny][nxp] (x fastest, rows
 // padded to nxp = round_up(nx, 32) elements so that every row starts on a
 // 128-byte boundary).  Deviation storage keeps g_i = f_i - W_i rho0.
-// All arithmetic is done in deviation variables (rho0 = 0 for plain
-// storage), so the same code serves FP64, FP32 and the FP32/FP16
-// deviation forms.
+// All arithmetic is done in deviation variables (rho0 = 0 for FP64
+// storage, 1 for the FP32 and FP16 forms; plain FP32 storage keeps each
+// population as its exact difference from the FP32 weight), so the same
+// code serves FP64, FP32 and the FP32/FP16 deviation forms.
 #pragma once
 
 #include <cstdint>
@@ -73,6 +74,7 @@ struct Params {
     int k;
     int bc[4];
     double rho_in, ux_in, uy_in;
+    double gin[9];            // inlet populations f*(rho_in, u_in) in FP64, as the storage holds them
     int ox0, oy0, ow, oh;
     const void* src;          // post-collision populations of step t-1 (or pre-collision if prestream)
     void* dst;                // post-collision populations of step t
@@ -96,8 +98,9 @@ struct Params {
     const long long* replay_off;
     const int* replay_idx;
     long long replay_t0, replay_n;
-    // precision form: FP64 recheck of dS within a relative band around delta
+    // precision form: FP64 recheck of dS within recheck_band of delta
     int recheck;
+    double recheck_band;
     // energy form
     const float* mlp;         // device copy of the network (FP32 master; rounded to BF16 at use)
     unsigned long long* newton_stats;   // it32, it64, sites, fails
@@ -118,19 +121,39 @@ template <int Q, typename T> struct PopArr { T v[Q]; };
 // ---------------------------------------------------------------------------
 // Storage traits: load / store a population as a deviation in type T.
 // ---------------------------------------------------------------------------
+// kProject: the collision removes the rounding defects of the conserved
+// moments of f - f* (conserve_neq below) -- FP32 storage, whose arithmetic
+// error would otherwise exceed the storage rounding; FP64 arithmetic is
+// exact enough, and FP16 storage rounding dominates its FP32 arithmetic.
+// kPlain: plain FP32 storage (plain32): each population f is held as an FP32
+// value, kept in the buffer as its exact difference g = f - fl32(W_i) from
+// the FP32 weight, so that the FP32 arithmetic works on deviations for
+// every FP32 form.
+struct plain32 {
+    float v;
+};
 template <typename S> struct Store;
 template <> struct Store<double> {
     using T = double;
+    static constexpr bool kProject = false, kPlain = false;
     __device__ static T load(const void* p, long long i) { return static_cast<const double*>(p)[i]; }
     __device__ static void store(void* p, long long i, T v) { static_cast<double*>(p)[i] = v; }
 };
 template <> struct Store<float> {
     using T = float;
+    static constexpr bool kProject = true, kPlain = false;
+    __device__ static T load(const void* p, long long i) { return static_cast<const float*>(p)[i]; }
+    __device__ static void store(void* p, long long i, T v) { static_cast<float*>(p)[i] = v; }
+};
+template <> struct Store<plain32> {
+    using T = float;
+    static constexpr bool kProject = true, kPlain = true;
     __device__ static T load(const void* p, long long i) { return static_cast<const float*>(p)[i]; }
     __device__ static void store(void* p, long long i, T v) { static_cast<float*>(p)[i] = v; }
 };
 template <> struct Store<__half> {
     using T = float;
+    static constexpr bool kProject = false, kPlain = false;
     __device__ static T load(const void* p, long long i) {
         return __half2float(static_cast<const __half*>(p)[i]);
     }
@@ -155,13 +178,13 @@ __device__ __forceinline__ bool is_solid(const Params& P, int x, int y) {
 // The library is compiled without automatic multiply-add contraction; every
 // fused multiply-add is written out, so each kernel that evaluates these
 // functions produces the same bits (bit-exact checkpoint / resume).
-template <typename T> __device__ __forceinline__ T dfma(T a, T b, T c);
-template <> __device__ __forceinline__ float dfma<float>(float a, float b, float c) { return fmaf(a, b, c); }
-template <> __device__ __forceinline__ double dfma<double>(double a, double b, double c) { return fma(a, b, c); }
+template <typename T> __host__ __device__ __forceinline__ T dfma(T a, T b, T c);
+template <> __host__ __device__ __forceinline__ float dfma<float>(float a, float b, float c) { return fmaf(a, b, c); }
+template <> __host__ __device__ __forceinline__ double dfma<double>(double a, double b, double c) { return fma(a, b, c); }
 
 // v . u for lattice velocity components in {-1, 0, 1}: additions only.
 template <typename L, typename T>
-__device__ __forceinline__ T cdotu(int i, T ux, T uy) {
+__host__ __device__ __forceinline__ T cdotu(int i, T ux, T uy) {
     const T a = L::cx(i) == 1 ? ux : (L::cx(i) == -1 ? -ux : T(0));
     const T b = L::cy(i) == 1 ? uy : (L::cy(i) == -1 ? -uy : T(0));
     return a + b;
@@ -171,7 +194,7 @@ __device__ __forceinline__ T cdotu(int i, T ux, T uy) {
 // pair is evaluated once: gs = W (c0 + 9/2 rho (v.u)^2) +- W 3 rho (v.u),
 // c0 = drho - 3/2 rho u^2.
 template <typename L, typename T>
-__device__ __forceinline__ void feq_poly(T drho, T rho, T ux, T uy, T* gs) {
+__host__ __device__ __forceinline__ void feq_poly(T drho, T rho, T ux, T uy, T* gs) {
     const T usq = dfma<T>(ux, ux, uy * uy);
     const T c0 = dfma<T>(T(-1.5) * rho, usq, drho);
     const T r45 = T(4.5) * rho, r3 = T(3) * rho;
@@ -203,16 +226,104 @@ template <> struct Par<double> {
     __device__ static double rho0(const Params& P) { return P.rho0; }
 };
 
-template <typename T> __device__ __forceinline__ T dsqrt(T x);
-template <> __device__ __forceinline__ float dsqrt<float>(float x) { return sqrtf(x); }
-template <> __device__ __forceinline__ double dsqrt<double>(double x) { return sqrt(x); }
+// ---------------------------------------------------------------------------
+// Stored values and the deviations the arithmetic works on.  FP64 storage
+// holds f (rho0 = 0); FP32 / FP16 deviation storage holds g = f - W_i rho0
+// (rho0 = 1); plain FP32 storage holds the FP32 value of f, kept as the
+// exact difference g = f - fl32(W_i).  FP32 arithmetic takes rho0 = 1 for
+// every FP32 / FP16 form.
+// ---------------------------------------------------------------------------
+
+// FP64 value of population i whose stored deviation is g.
+template <typename L, typename S>
+__device__ __forceinline__ double pop_f64(const Params& P, int i, typename Store<S>::T g) {
+    if constexpr (Store<S>::kPlain) return (double)g + (double)(float)L::w(i);
+    else return (double)g + L::w(i) * P.rho0;
+}
+
+// Deviation of a population whose value f was computed in FP64 (initial and
+// imported states), as a stored field holds it: plain FP32 rounds f, the
+// deviation forms round f - W_i rho0.
+template <typename L, typename S>
+__device__ __forceinline__ typename Store<S>::T dev_of_f64(const Params& P, int i, double f) {
+    using T = typename Store<S>::T;
+    if constexpr (Store<S>::kPlain) return (float)f - (float)L::w(i);
+    else return (T)(f - L::w(i) * P.rho0);
+}
+
+// A deviation computed in the arithmetic, rounded as the storage rounds it:
+// plain FP32 storage rounds f = g + fl32(W_i) to FP32 (the difference with
+// fl32(W_i) is then exact when f lies within a factor two of W_i); the other
+// forms round at the store itself.
+template <typename L, typename S>
+__device__ __forceinline__ typename Store<S>::T store_round(int i, typename Store<S>::T g) {
+    if constexpr (Store<S>::kPlain) {
+        const float w = (float)L::w(i);
+        return (g + w) - w;
+    } else {
+        (void)i;
+        return g;
+    }
+}
+
+// Conserved moments of the nonequilibrium part d = f - f*: zero in exact
+// arithmetic, since f* has the conserved moments of f (mass and momentum
+// (lbgkLB), and the energy 2E for the energy-constrained quasiequilibrium,
+// Sec. 3.3).  The FP32 evaluation of f* leaves errors of a few ulps in each
+// f*_i, whose sums the over-relaxed collision f' = f - 2 beta d (beta ~ 1)
+// would turn into a drift of the conserved quantities by about twice their
+// value per step, the same at every site of a smooth flow.  They are removed
+// by subtracting the combination W_i (a + b . v_i + e |v_i|^2) of the
+// collision invariants that has the same moments as d (D2Q9: sum W = 1,
+// sum W v v = I/3, sum W |v|^2 = 2/3, sum W |v|^4 = 8/9; e = 0 without the
+// energy constraint; D1Q3: sum W v^2 = 1/3).  The sums are of the small
+// nonequilibrium parts, so the conserved moments of the result are exact to
+// their rounding; in exact arithmetic nothing changes.
+template <typename L, int EQ>
+__device__ __forceinline__ void conserve_neq(float* d) {
+    if constexpr (L::Q == 9) {
+        const float D0 = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
+        const float Dx = ((d[1] - d[3]) + (d[5] - d[6])) + (d[8] - d[7]);
+        const float Dy = ((d[2] - d[4]) + (d[5] - d[8])) + (d[6] - d[7]);
+        float a = D0, e = 0.0f;
+        if constexpr (EQ >= EQ_ENERGY) {
+            const float DE = ((d[1] + d[2]) + (d[3] + d[4])) + 2.0f * ((d[5] + d[6]) + (d[7] + d[8]));
+            a = fmaf(-1.5f, DE, 2.0f * D0);     // a = 2 D0 - 3/2 DE
+            e = fmaf(2.25f, DE, -1.5f * D0);    // e = 9/4 DE - 3/2 D0
+        }
+        // W_i (a + 3 v_i . D + e |v_i|^2), weights 4/9, 1/9, 1/36
+        const float m1 = (a + e) * (1.0f / 9.0f), px = Dx * (1.0f / 3.0f), py = Dy * (1.0f / 3.0f);
+        const float m5 = fmaf(2.0f, e, a) * (1.0f / 36.0f), qx = Dx * (1.0f / 12.0f), qy = Dy * (1.0f / 12.0f);
+        d[0] -= a * (4.0f / 9.0f);
+        d[1] -= m1 + px;
+        d[3] -= m1 - px;
+        d[2] -= m1 + py;
+        d[4] -= m1 - py;
+        const float s1 = m5 + qy, s2 = m5 - qy;
+        d[5] -= s1 + qx;
+        d[6] -= s1 - qx;
+        d[7] -= s2 - qx;
+        d[8] -= s2 + qx;
+    } else {
+        const float D0 = (d[0] + d[1]) + d[2];
+        const float Dx = d[2] - d[1];
+        const float m = D0 * (1.0f / 6.0f), p = Dx * 0.5f;   // W (D0 + 3 v Dx), W = 1/6
+        d[0] -= D0 * (2.0f / 3.0f);
+        d[1] -= m - p;
+        d[2] -= m + p;
+    }
+}
+
+template <typename T> __host__ __device__ __forceinline__ T dsqrt(T x);
+template <> __host__ __device__ __forceinline__ float dsqrt<float>(float x) { return sqrtf(x); }
+template <> __host__ __device__ __forceinline__ double dsqrt<double>(double x) { return sqrt(x); }
 
 // Entropic for mass and momentum.  D1Q3: closed form of Sec. 4.1 with the
 // left/right labels read so that the momentum is +rho u (rest
 // (2 rho/3)(2 - s), left (rho/6)(2s - 3u - 1), right (rho/6)(3u - 1 + 2s),
 // s = sqrt(1 + 3u^2)).  D2Q9: product formula of Sec. 4.2.
 template <typename L, typename T>
-__device__ __forceinline__ void feq_entropic(T rho, T ux, T uy, T rho0, T* gs) {
+__host__ __device__ __forceinline__ void feq_entropic(T rho, T ux, T uy, T rho0, T* gs) {
     if constexpr (L::Q == 3) {
         const T s = dsqrt<T>(T(1) + T(3) * ux * ux);
         gs[0] = T(2) * rho / T(3) * (T(2) - s) - T(L::w(0)) * rho0;
@@ -240,7 +351,7 @@ __device__ __forceinline__ void feq_entropic(T rho, T ux, T uy, T rho0, T* gs) {
 // energy forms use the isothermal entropic formula, whose energy
 // multiplier is zero).
 template <typename L, typename T>
-__device__ __forceinline__ void feq_rho_u(int eq, T rho, T ux, T uy, T rho0, T* gs) {
+__host__ __device__ __forceinline__ void feq_rho_u(int eq, T rho, T ux, T uy, T rho0, T* gs) {
     if (eq == EQ_POLY) feq_poly<L, T>(rho - rho0, rho, ux, uy, gs);
     else feq_entropic<L, T>(rho, ux, uy, rho0, gs);
 }
@@ -292,8 +403,15 @@ template <> __device__ __forceinline__ double phi_fn<double>(double x) {
     return fma(1.0 + x, log1p(x), -x);
 }
 
+// 1 / x: FP32 from the hardware approximation refined by one Newton-Raphson
+// step r + r (1 - x r) (the relative error e of the seed becomes ~e^2, below
+// one ulp); FP64 divides.
 template <typename T> __device__ __forceinline__ T recip(T x);
-template <> __device__ __forceinline__ float recip<float>(float x) { return __frcp_rn(x); }
+template <> __device__ __forceinline__ float recip<float>(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return fmaf(r, fmaf(-x, r, 1.0f), r);
+}
 template <> __device__ __forceinline__ double recip<double>(double x) { return 1.0 / x; }
 
 // Exact dS of one site in type T; +inf outside the positive cone.
@@ -396,10 +514,45 @@ __device__ __forceinline__ void diffuse_wall(unsigned mask, T* g) {
         if ((mask >> i) & 1u) g[i] = T(L::w(i)) * rho_w;
 }
 
+// Quasiequilibrium f*(rho, u) evaluated in FP64 and held as the storage
+// holds a population (dev_of_f64): the initial state.
+template <typename L, typename S>
+__device__ __forceinline__ void bc_equilibrium(const Params& P, double rho, double ux, double uy,
+                                               typename Store<S>::T* g) {
+    double fs[L::Q];
+    feq_rho_u<L, double>(P.eq, rho, ux, uy, 0.0, fs);
+#pragma unroll
+    for (int i = 0; i < L::Q; i++) g[i] = dev_of_f64<L, S>(P, i, fs[i]);
+}
+
+// Outlet rule of Sec. 4.2: the quasiequilibrium of the density and velocity
+// of column nx - 2 (stored deviations v), in the run's arithmetic (the
+// callers round it as the storage holds a population).
+template <typename L, typename T>
+__device__ __forceinline__ void outlet_equilibrium(const Params& P, const T* v, T* g) {
+    const T rho0 = Par<T>::rho0(P);
+    T drho = T(0), jx = T(0), jy = T(0);
+#pragma unroll
+    for (int j = 0; j < L::Q; j++) {
+        drho += v[j];
+        jx += T(L::cx(j)) * v[j];
+        jy += T(L::cy(j)) * v[j];
+    }
+    const T rho = rho0 + drho;
+    feq_rho_u<L, T>(P.eq, rho, jx / rho, jy / rho, rho0, g);
+}
+
+// Inlet rule of Sec. 4.2: the quasiequilibrium of the free stream, computed
+// once in FP64 by the host (Params::gin).
+template <typename L, typename T>
+__device__ __forceinline__ void inlet_equilibrium(const Params& P, T* g) {
+#pragma unroll
+    for (int i = 0; i < L::Q; i++) g[i] = (T)P.gin[i];
+}
+
 template <typename L, typename S>
 __device__ void gather_site(const Params& P, int x, int y, typename Store<S>::T* g) {
     using T = typename Store<S>::T;
-    const T rho0 = Par<T>::rho0(P);
     const long long s0 = (long long)y * P.nxp + x;
     if (P.prestream) {
 #pragma unroll
@@ -419,7 +572,7 @@ __device__ void gather_site(const Params& P, int x, int y, typename Store<S>::T*
                 sx = sx < 0 ? sx + P.nx : sx - P.nx;
             } else if (kind == BC_INLET) {
                 if (!have_in) {
-                    feq_rho_u<L, T>(P.eq, (T)P.rho_in, (T)P.ux_in, (T)P.uy_in, rho0, gin);
+                    inlet_equilibrium<L, T>(P, gin);
                     have_in = true;
                 }
                 g[i] = gin[i];
@@ -427,14 +580,12 @@ __device__ void gather_site(const Params& P, int x, int y, typename Store<S>::T*
             } else if (kind == BC_OUTLET) {
                 if (!have_out) {
                     const long long sp = (long long)y * P.nxp + (P.nx - 2);
-                    T drho = T(0), jx = T(0), jy = T(0);
+                    T v[L::Q];
 #pragma unroll
-                    for (int j = 0; j < L::Q; j++) {
-                        const T v = Store<S>::load(P.src, j * P.plane + sp);
-                        drho += v; jx += T(L::cx(j)) * v; jy += T(L::cy(j)) * v;
-                    }
-                    const T rho = rho0 + drho;
-                    feq_rho_u<L, T>(P.eq, rho, jx / rho, jy / rho, rho0, gout);
+                    for (int j = 0; j < L::Q; j++) v[j] = Store<S>::load(P.src, j * P.plane + sp);
+                    outlet_equilibrium<L, T>(P, v, gout);
+#pragma unroll
+                    for (int j = 0; j < L::Q; j++) gout[j] = store_round<L, S>(j, gout[j]);
                     have_out = true;
                 }
                 g[i] = gout[i];

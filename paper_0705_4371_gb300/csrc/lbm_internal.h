@@ -23,14 +23,16 @@ struct Launchers {
     cudaError_t (*occupancy)(int tile_shape, int* blocks_per_sm);
 };
 
-// storage: 0 = FP64, 1 = FP32 (plain and deviation), 2 = FP16 deviation
+// storage: FP64, FP32 deviation, FP16 deviation, plain FP32 (f32p)
 Launchers launchers_f64(int lattice, int eq);
 Launchers launchers_f32(int lattice, int eq);
 Launchers launchers_f16(int lattice, int eq);
+Launchers launchers_f32p(int lattice, int eq);
 // energy-constrained equilibria (D2Q9), one translation unit per storage
 Launchers launchers_f64_energy(int eq);
 Launchers launchers_f32_energy(int eq);
 Launchers launchers_f16_energy(int eq);
+Launchers launchers_f32p_energy(int eq);
 
 constexpr int kTileShapes = 7;   // tile shapes of the D2Q9 stream-collide kernel
 
@@ -81,11 +83,13 @@ struct BatchLaunchers {
 // stream-collide kernel, in concurrent branches (one stream per run).
 constexpr int kBatchVariants = 3;
 constexpr int kBatchKernelVariants = 2;
-// storage: 0 = FP64, 1 = FP32, 2 = FP16; eq: EQ_POLY or EQ_ENTROPIC
+// storage: 0 = FP64, 1 = FP32 deviation, 2 = FP16 deviation, 3 = plain
+// FP32; eq: EQ_POLY or EQ_ENTROPIC
 BatchLaunchers batch_launchers(int storage, int eq, int variant);
 BatchLaunchers batch_launchers_f64(int eq, int variant);
 BatchLaunchers batch_launchers_f32(int eq, int variant);
 BatchLaunchers batch_launchers_f16(int eq, int variant);
+BatchLaunchers batch_launchers_f32p(int eq, int variant);
 
 // A run as the batch sees it (lbm_api.cu).
 struct RunView {

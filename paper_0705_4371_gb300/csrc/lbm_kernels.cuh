@@ -89,7 +89,7 @@ __device__ __forceinline__ void moments(const T* g, T rho0, T& drho, T& rho, T& 
 }
 
 // u = j / rho: FP64 divides (as the oracle does); FP32 multiplies by the
-// correctly rounded reciprocal.
+// refined reciprocal (recip).
 template <typename T>
 __device__ __forceinline__ void velocity(T jx, T jy, T rho, T& ux, T& uy) {
     if constexpr (sizeof(T) == 8) {
@@ -327,7 +327,10 @@ __device__ __noinline__ T elbm_factor(PopArr<L::Q, T> g, PopArr<L::Q, T> gs, T r
 }
 
 // PROBE = false: the caller guarantees the site is not the probe site.
-template <typename L, typename T, int EQ, bool PROBE = true>
+// PROJ: remove the rounding defects of the conserved moments of f - f*
+// (conserve_neq; FP32 storage).  g leaves as the deviations to store, before
+// the storage's rounding (store_round).
+template <typename L, typename T, int EQ, bool PROJ, bool PROBE = true>
 __device__ __forceinline__ bool update_site(const Params& P, T* g, int x, int y, long long t,
                                             bool& nonfinite, NewtonCount& nc,
                                             const float* a0 = nullptr) {
@@ -339,6 +342,7 @@ __device__ __forceinline__ bool update_site(const Params& P, T* g, int x, int y,
     T d[L::Q];
 #pragma unroll
     for (int i = 0; i < L::Q; i++) d[i] = g[i] - gs[i];
+    if constexpr (PROJ) conserve_neq<L, EQ>(d);
     const bool pending =
         P.k > 0 && !ds_cleared<L, T, EQ>(d, gs, rho, ux, uy, Par<T>::rho0(P), Par<T>::delta(P));
     T nb2 = T(-2) * Par<T>::beta(P);
@@ -389,9 +393,10 @@ template <> struct MlpSlot<EQ_ENERGY_MLP> {
 
 // Exact dS of site (x, y) from the source field (the pre-collision state is
 // re-gathered; the source is not written during a step).  The precision
-// form decides the sites within 1e-3 of delta in FP64; the value kept for
-// ranking then stays on the same side of delta.  Returns dS in T (NaN for a
-// non-finite state).
+// form decides the sites whose FP32 dS lies within recheck_band of delta
+// (a bound on the FP32 evaluation error of dS, set by the host) in FP64;
+// the value kept for ranking then stays on the same side of delta.  Returns
+// dS in T (NaN for a non-finite state).
 template <typename L, typename S, int EQ>
 __device__ __noinline__ typename Store<S>::T resolve_ds(const Params& P, int x, int y) {
     using T = typename Store<S>::T;
@@ -399,7 +404,7 @@ __device__ __noinline__ typename Store<S>::T resolve_ds(const Params& P, int x, 
     gather_site<L, S>(P, x, y, g);
     site_equilibrium<L, T, EQ>(P, g, gs, rho, ux, uy);
     T ds = delta_s_exact<L, T>(g, gs, Par<T>::rho0(P));
-    if (P.recheck && isfinite(ds) && fabs((double)ds - P.delta) <= 1e-3 * fabs(P.delta)) {
+    if (P.recheck && isfinite(ds) && fabs((double)ds - P.delta) <= P.recheck_band) {
         PopArr<L::Q, T> ga;
 #pragma unroll
         for (int i = 0; i < L::Q; i++) ga.v[i] = g[i];
@@ -427,6 +432,114 @@ __device__ __forceinline__ void warp_push(const Params& P, bool cand, T ds, unsi
         P.cand_key[slot] = ds_key((double)ds);
         P.cand_idx[slot] = site;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Block stage of the selection (k sites of the whole grid are selected, so a
+// block never contributes more than its own k best): a block holds its
+// candidates in shared memory, cuts them to its k largest (dS, -index) with
+// the block radix select whenever the buffer fills, and flushes what it kept
+// to the global list when it ends.  The global select then ranks at most
+// k x blocks keys.  With k too large for a cut to free room, the block
+// flushes its buffer to the global list instead (which holds one slot per
+// site and cannot overflow).
+// ---------------------------------------------------------------------------
+constexpr int kBlockCand = 512;
+
+struct BlockCand {
+    unsigned long long key[kBlockCand];
+    unsigned idx[kBlockCand];
+    unsigned n;          // candidates appended (entries beyond kBlockCand went to the global list)
+    unsigned base;
+};
+
+// Warp-level append to the block's buffer (every lane calls).
+template <typename T>
+__device__ __forceinline__ void block_push(const Params& P, BlockCand& bc, bool cand, T ds, unsigned site) {
+    const unsigned m = __ballot_sync(0xffffffffu, cand);
+    if (m == 0) return;
+    const int lane = threadIdx.x & 31;
+    unsigned base = 0;
+    if (lane == 0) base = atomicAdd(&bc.n, (unsigned)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (cand) {
+        const unsigned slot = base + __popc(m & ((1u << lane) - 1u));
+        const unsigned long long key = ds_key((double)ds);
+        if (slot < (unsigned)kBlockCand) {
+            bc.key[slot] = key;
+            bc.idx[slot] = site;
+        } else {
+            // no room (the callers cut or flush before it can happen)
+            const unsigned g = atomicAdd(P.cand_count, 1u);
+            P.cand_key[g] = key;
+            P.cand_idx[g] = site;
+        }
+    }
+}
+
+// Keep the k best of the buffer (all threads call; blockDim >= 128).
+static __device__ __noinline__ void block_cut(BlockCand& bc, TopkScratch& sc, int k) {
+    constexpr int kPer = kBlockCand / 128;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    __syncthreads();
+    const int n = (int)min(bc.n, (unsigned)kBlockCand);
+    if (n <= k) return;   // uniform: n was read after the barrier
+    const Thresh th = block_topk(sc, n, k, [&](int e) { return bc.key[e]; }, [&](int e) { return bc.idx[e]; });
+    unsigned long long kk[kPer];
+    unsigned ii[kPer];
+    bool keep[kPer];
+#pragma unroll
+    for (int r = 0; r < kPer; r++) {
+        const int e = tid + r * nt;
+        keep[r] = e < n && th.selected(bc.key[e], bc.idx[e]);
+        kk[r] = keep[r] ? bc.key[e] : 0ull;
+        ii[r] = keep[r] ? bc.idx[e] : 0u;
+    }
+    __syncthreads();
+    if (tid == 0) bc.n = 0;
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kPer; r++) {
+        if (keep[r]) {
+            const unsigned slot = atomicAdd(&bc.n, 1u);
+            bc.key[slot] = kk[r];
+            bc.idx[slot] = ii[r];
+        }
+    }
+    __syncthreads();
+}
+
+// Move the buffer to the global candidate list (all threads call).
+static __device__ __noinline__ void block_flush(const Params& P, BlockCand& bc) {
+    __syncthreads();
+    const int n = (int)min(bc.n, (unsigned)kBlockCand);
+    if (n == 0) return;   // uniform
+    if (threadIdx.x == 0) bc.base = atomicAdd(P.cand_count, (unsigned)n);
+    __syncthreads();
+    const unsigned base = bc.base;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        P.cand_key[base + e] = bc.key[e];
+        P.cand_idx[base + e] = bc.idx[e];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) bc.n = 0;
+    __syncthreads();
+}
+
+// Make room for another blockDim candidates (all threads call).
+__device__ __forceinline__ void block_room(const Params& P, BlockCand& bc, TopkScratch& sc) {
+    __syncthreads();
+    const int room = kBlockCand - (int)blockDim.x;
+    if ((int)bc.n > room) {   // uniform
+        if (P.k <= room) block_cut(bc, sc, P.k);
+        else block_flush(P, bc);
+    }
+}
+
+// What the block contributes to the global select: its k best (all threads).
+__device__ __forceinline__ void block_finish(const Params& P, BlockCand& bc, TopkScratch& sc) {
+    if (P.k > 0) block_cut(bc, sc, P.k);
+    block_flush(P, bc);
 }
 
 // ---------------------------------------------------------------------------
@@ -502,9 +615,20 @@ __device__ __noinline__ void select_and_fix(const Params& P, SelectShared& ss,
             T g[L::Q], gs[L::Q], rho, ux, uy;
             gather_site<L, S>(P, x, y, g);
             site_equilibrium<L, T, EQ>(P, g, gs, rho, ux, uy);
+            if constexpr (Store<S>::kProject) {
+                // f' = f* = f - (f - f*), with the conserved moments of
+                // f - f* freed of rounding as in the collision
+                T d[L::Q];
+#pragma unroll
+                for (int i = 0; i < L::Q; i++) d[i] = g[i] - gs[i];
+                conserve_neq<L, EQ>(d);
+#pragma unroll
+                for (int i = 0; i < L::Q; i++) gs[i] = g[i] - d[i];
+            }
             const long long o = (long long)y * P.nxp + x;
 #pragma unroll
-            for (int i = 0; i < L::Q; i++) Store<S>::store(P.dst, i * P.plane + o, gs[i]);
+            for (int i = 0; i < L::Q; i++)
+                Store<S>::store(P.dst, i * P.plane + o, store_round<L, S>(i, gs[i]));
         }
     }
     __syncthreads();
@@ -530,6 +654,7 @@ struct FinishShared {
     unsigned long long key[kStage];
     unsigned idx[kStage];
     unsigned pend[kPend];
+    BlockCand bc;
     unsigned npend;
     int is_last;
 };
@@ -553,12 +678,15 @@ __device__ __forceinline__ void warp_pend(const Params& P, FinishShared& fs, boo
     warp_pend(P, fs.pend, &fs.npend, pend, site);
 }
 
-// Exact dS of n pending sites, appending the candidates; all threads call.
+// Exact dS of n pending sites, appending the candidates to the block's
+// buffer bc (its k best reach the global list) or, with bc null, straight
+// to the global list; all threads call with the same n.
 template <typename L, typename S, int EQ, typename SiteAt>
-__device__ void resolve_list(const Params& P, int n, SiteAt site_at) {
+__device__ void resolve_list(const Params& P, int n, SiteAt site_at, BlockCand* bc, TopkScratch* sc) {
     using T = typename Store<S>::T;
     const T delta = Par<T>::delta(P);
     for (int b = 0; b < n; b += blockDim.x) {
+        if (bc) block_room(P, *bc, *sc);
         const int j = b + (int)threadIdx.x;
         unsigned site = 0;
         T ds = T(-1);
@@ -566,17 +694,19 @@ __device__ void resolve_list(const Params& P, int n, SiteAt site_at) {
             site = site_at(j);
             ds = resolve_ds<L, S, EQ>(P, (int)(site % (unsigned)P.nx), (int)(site / (unsigned)P.nx));
         }
-        warp_push<T>(P, ds > delta, ds, site);
+        if (bc) block_push<T>(P, *bc, ds > delta, ds, site);
+        else warp_push<T>(P, ds > delta, ds, site);
     }
 }
 
 template <typename L, typename S, int EQ>
 __device__ __forceinline__ void finish_parts(const Params& P, const unsigned* pend, unsigned npend,
-                                             int& is_last, SelectShared& ss,
+                                             int& is_last, SelectShared& ss, BlockCand& bc,
                                              unsigned long long* stage_key, unsigned* stage_idx,
                                              int stage_cap) {
     const int np = (int)min(npend, (unsigned)kPend);
-    if (np > 0) resolve_list<L, S, EQ>(P, np, [&](int j) { return pend[j]; });
+    if (np > 0) resolve_list<L, S, EQ>(P, np, [&](int j) { return pend[j]; }, &bc, &ss.sc);
+    block_finish(P, bc, ss.sc);
     // the barrier makes the block's writes visible to thread 0, whose
     // device-scope fence then orders all of them before the ticket
     __syncthreads();
@@ -591,7 +721,8 @@ __device__ __forceinline__ void finish_parts(const Params& P, const unsigned* pe
     if (is_last) {
         const int ng = (int)__ldcg(P.pend_count);
         if (ng > 0) {
-            resolve_list<L, S, EQ>(P, ng, [&](int j) { return __ldcg(P.pend_idx + j); });
+            resolve_list<L, S, EQ>(P, ng, [&](int j) { return __ldcg(P.pend_idx + j); }, &bc, &ss.sc);
+            block_finish(P, bc, ss.sc);
             __syncthreads();
             if (threadIdx.x == 0) *P.pend_count = 0;
         }
@@ -607,7 +738,7 @@ __device__ __forceinline__ void finish_parts(const Params& P, const unsigned* pe
 template <typename L, typename S, int EQ>
 __device__ __forceinline__ void finish_block(const Params& P, FinishShared& fs) {
     __syncthreads();
-    finish_parts<L, S, EQ>(P, fs.pend, fs.npend, fs.is_last, fs.ss, fs.key, fs.idx, kStage);
+    finish_parts<L, S, EQ>(P, fs.pend, fs.npend, fs.is_last, fs.ss, fs.bc, fs.key, fs.idx, kStage);
 }
 
 // Boundary site (or any site of the first step after a state upload): gather
@@ -626,7 +757,9 @@ __device__ __noinline__ int boundary_site(const Params& P, int x, int y, long lo
         for (int i = 0; i < L::Q; i++) g[i] = T(0);
     } else {
         gather_site<L, S>(P, x, y, g);
-        pending = update_site<L, T, EQ>(P, g, x, y, t, nonfinite, nc);
+        pending = update_site<L, T, EQ, Store<S>::kProject>(P, g, x, y, t, nonfinite, nc);
+#pragma unroll
+        for (int i = 0; i < L::Q; i++) g[i] = store_round<L, S>(i, g[i]);
     }
     if constexpr (EQ >= EQ_ENERGY) {
         if (nc.sites) {
@@ -723,6 +856,15 @@ template <> struct VecIO<__half, 2> {
     }
 };
 
+template <> struct VecIO<plain32, 4> {
+    __device__ static void load(const void* p, long long i, float* v) { VecIO<float, 4>::load(p, i, v); }
+    __device__ static void store(void* p, long long i, const float* v) { VecIO<float, 4>::store(p, i, v); }
+};
+template <> struct VecIO<plain32, 2> {
+    __device__ static void load(const void* p, long long i, float* v) { VecIO<float, 2>::load(p, i, v); }
+    __device__ static void store(void* p, long long i, const float* v) { VecIO<float, 2>::store(p, i, v); }
+};
+
 // Interior-path accessors with 32-bit element indices (every population
 // array holds fewer than 2^31 elements; checked at creation).
 template <typename S, int VEC>
@@ -764,7 +906,10 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_collide_d2q9(const __grid_
     __shared__ FinishShared fs;
     __shared__ MlpSlot<EQ> mslot;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) fs.npend = 0;
+    if (threadIdx.x == 0) {
+        fs.npend = 0;
+        fs.bc.n = 0;
+    }
     mslot.fill(P);
     __syncthreads();
     const long long t = *P.step;
@@ -819,16 +964,18 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_collide_d2q9(const __grid_
                     // interior tile: every lane holds a fluid site
                     float a0[3];
                     mlp_site_start<T>(P, mslot.s, true, g[s], a0);
-                    pend[s] = update_site<L, T, EQ>(P, g[s], xs + s, y, t, nonfinite, nc, a0);
+                    pend[s] = update_site<L, T, EQ, Store<S>::kProject>(P, g[s], xs + s, y, t, nonfinite,
+                                                                         nc, a0);
                 } else {
-                    pend[s] = update_site<L, T, EQ>(P, g[s], xs + s, y, t, nonfinite, nc);
+                    pend[s] = update_site<L, T, EQ, Store<S>::kProject>(P, g[s], xs + s, y, t, nonfinite,
+                                                                         nc);
                 }
             }
 #pragma unroll
             for (int i = 0; i < L::Q; i++) {
                 T v[VEC];
 #pragma unroll
-                for (int s = 0; s < VEC; s++) v[s] = g[s][i];
+                for (int s = 0; s < VEC; s++) v[s] = store_round<L, S>(i, g[s][i]);
                 store_vec<S, VEC>(dst, i * plane + row, v);
             }
 #pragma unroll
@@ -869,7 +1016,7 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_collide_d2q9(const __grid_
             __syncthreads();
             if (fs.npend > (unsigned)(kPend - TX * WARPS)) {
                 resolve_list<L, S, EQ>(P, (int)min(fs.npend, (unsigned)kPend),
-                                       [&](int j) { return fs.pend[j]; });
+                                       [&](int j) { return fs.pend[j]; }, &fs.bc, &fs.ss.sc);
                 __syncthreads();
                 if (threadIdx.x == 0) fs.npend = 0;
                 __syncthreads();
@@ -883,18 +1030,20 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_collide_d2q9(const __grid_
 
 // ---------------------------------------------------------------------------
 // K1 for D2Q9 with tiles staged in shared memory by the tensor memory
-// accelerator.  A block tile is R rows x 128 sites; for each of the 9
-// population planes one 3-D bulk tensor copy brings rows y0 - 1 .. y0 + R
-// and columns x0 - H .. x0 + 128 + H (H elements = 16 bytes on each side,
-// which keeps every copy 16-byte aligned), i.e. every source any boundary
-// rule of the tile can need (except a periodic wrap).  Copies complete on an
-// mbarrier; STAGES tiles are in flight per block, so the bytes in flight do
-// not depend on registers.  Warp w computes row w of the tile, lane l the
-// sites x0 + l + 32 s (s = 0..3): shared-memory reads and global stores are
-// both consecutive across the warp.  In tiles that touch a boundary or the
-// obstacle the sites use the rule-by-rule gather from shared memory.  Every
-// wait on an mbarrier is bounded: on expiry the block flags ERR_TIMEOUT,
-// stops issuing copies, waits (bounded) for the copies it issued, and ends.
+// accelerator.  A block tile is R rows x 128 sites.  Population i at row y
+// comes from row y - v_iy of the source field, so for each of the 9 planes
+// one 3-D bulk tensor copy brings exactly the R rows y0 - v_iy ..
+// y0 - v_iy + R - 1 the tile pulls from that plane, over columns x0 - H ..
+// x0 + 128 + H (H elements = 16 bytes on each side, which keeps every copy
+// 16-byte aligned).  Copies complete on an mbarrier; STAGES tiles are in
+// flight per block, so the bytes in flight do not depend on registers.
+// Warp w computes row w of the tile, lane l the sites x0 + l + 32 s
+// (s = 0..3): shared-memory reads and global stores are both consecutive
+// across the warp.  In tiles that touch a boundary or the obstacle the sites
+// use the rule-by-rule gather, from shared memory where the source lies in
+// its plane's window and from the source field otherwise.  Every wait on an
+// mbarrier is bounded: on expiry the block flags ERR_TIMEOUT, stops issuing
+// copies, waits (bounded) for the copies it issued, and ends.
 // ---------------------------------------------------------------------------
 constexpr int kTmaTX = 128;
 constexpr long long kWaitLimit = 1ll << 22;   // try_wait polls before a wait is declared failed
@@ -940,7 +1089,7 @@ template <typename S, int R, int TX = kTmaTX>
 struct TmaLayout {
     static constexpr int H = 16 / (int)sizeof(S);          // halo columns (16 bytes)
     static constexpr int W = TX + 2 * H;                   // staged row length
-    static constexpr int ROWS = R + 2;                     // staged rows: y0 - 1 .. y0 + R
+    static constexpr int ROWS = R;                         // plane i: rows y0 - v_iy .. y0 - v_iy + R - 1
     static constexpr int BOX_BYTES = ROWS * W * (int)sizeof(S);
     static constexpr int PLANE_BYTES = (BOX_BYTES + 127) / 128 * 128;   // 128-byte aligned boxes
     static constexpr int PLANE = PLANE_BYTES / (int)sizeof(S);
@@ -951,6 +1100,7 @@ struct TmaLayout {
 struct TmaShared {
     SelectShared ss;
     unsigned pend[kPend];
+    BlockCand bc;
     unsigned npend;
     int is_last;
     int abort;
@@ -963,20 +1113,25 @@ constexpr size_t tma_smem_bytes() {
            (EQ == EQ_ENERGY_MLP ? sizeof(MlpSlot<EQ>) + 16 : 0);
 }
 
-// Pre-collision deviations of site (x, y) of a staged tile, from shared
-// memory: the same rules as gather_site (free flight, Sec. 4.2 boundaries),
-// reading box[i][row][col] with row = y - y0 + 1, col = x - x0 + H.  Not used
-// with periodic sides (their sources lie outside the box).
+// Pre-collision deviations of site (x, y) of a staged tile: the same rules
+// as gather_site (free flight, Sec. 4.2 boundaries).  Plane j's window holds
+// source rows y0 - v_jy .. y0 - v_jy + R - 1 (box[j][row][col] with
+// row = sy - y0 + v_jy, col = sx - x0 + H); a rule that reads a plane
+// outside its window (a bounce-back or a mirror at the tile's edge rows, the
+// outlet column) reads the source field instead.  Not used with periodic
+// sides.
 template <typename S, int R, int TX = kTmaTX>
 __device__ __forceinline__ void gather_site_smem(const Params& P, const S* box, int x0, int y0, int x,
                                                  int y, typename Store<S>::T* g) {
     using L = D2Q9;
     using T = typename Store<S>::T;
     using LY = TmaLayout<S, R, TX>;
-    auto at = [&](int i, int sx, int sy) {
-        return Store<S>::load(box + i * LY::PLANE + (sy - y0 + 1) * LY::W + (sx - x0 + LY::H), 0);
+    auto at = [&](int j, int sx, int sy) {
+        const int r = sy - y0 + L::cy(j), c = sx - x0 + LY::H;
+        if ((unsigned)r < (unsigned)R && (unsigned)c < (unsigned)LY::W)
+            return Store<S>::load(box + j * LY::PLANE + r * LY::W + c, 0);
+        return Store<S>::load(P.src, j * P.plane + (long long)sy * P.nxp + sx);
     };
-    const T rho0 = Par<T>::rho0(P);
     if (P.prestream) {
 #pragma unroll
         for (int i = 0; i < L::Q; i++) g[i] = at(i, x, y);
@@ -996,20 +1151,18 @@ __device__ __forceinline__ void gather_site_smem(const Params& P, const S* box, 
                 sx = x;   // the column beyond the side is a copy of the side column
             } else if (kind == BC_INLET) {
                 if (!have_in) {
-                    feq_rho_u<L, T>(P.eq, (T)P.rho_in, (T)P.ux_in, (T)P.uy_in, rho0, gin);
+                    inlet_equilibrium<L, T>(P, gin);
                     have_in = true;
                 }
                 g[i] = gin[i];
             } else if (kind == BC_OUTLET) {
                 if (!have_out) {
-                    T drho = T(0), jx = T(0), jy = T(0);
+                    T v[L::Q];
 #pragma unroll
-                    for (int j = 0; j < L::Q; j++) {
-                        const T v = at(j, P.nx - 2, y);
-                        drho += v; jx += T(L::cx(j)) * v; jy += T(L::cy(j)) * v;
-                    }
-                    const T rho = rho0 + drho;
-                    feq_rho_u<L, T>(P.eq, rho, jx / rho, jy / rho, rho0, gout);
+                    for (int j = 0; j < L::Q; j++) v[j] = at(j, P.nx - 2, y);
+                    outlet_equilibrium<L, T>(P, v, gout);
+#pragma unroll
+                    for (int j = 0; j < L::Q; j++) gout[j] = store_round<L, S>(j, gout[j]);
                     have_out = true;
                 }
                 g[i] = gout[i];
@@ -1048,7 +1201,7 @@ __device__ __noinline__ void tma_tile_general(const Params& P, const S* box, int
     const int nxp = P.nxp, plane = (int)P.plane;
     const bool periodic = P.bc[0] == BC_PERIODIC || P.bc[2] == BC_PERIODIC;
     const int y = y0 + warp;
-    const S* sb = box + (warp + 1) * LY::W + LY::H;
+    const S* sb = box + warp * LY::W + LY::H;
 #pragma unroll 1
     for (int s = 0; s < TX / 32; s++) {
         const int x = x0 + lane + 32 * s;
@@ -1073,8 +1226,7 @@ __device__ __noinline__ void tma_tile_general(const Params& P, const S* box, int
                 for (int i = 0; i < L::Q; i++) g[i] = T(0);
             } else if (shift) {
 #pragma unroll
-                for (int i = 0; i < L::Q; i++)
-                    g[i] = Store<S>::load(sb + i * LY::PLANE + c - L::cx(i) - L::cy(i) * LY::W, 0);
+                for (int i = 0; i < L::Q; i++) g[i] = Store<S>::load(sb + i * LY::PLANE + c - L::cx(i), 0);
             } else if (is_solid(P, x, y)) {
                 fluid = false;
 #pragma unroll
@@ -1088,13 +1240,14 @@ __device__ __noinline__ void tma_tile_general(const Params& P, const S* box, int
                 float a0[3];
                 __syncwarp();
                 mlp_site_start<T>(P, mslot.s, fluid, g, a0);
-                if (fluid) pend = update_site<L, T, EQ>(P, g, x, y, t, nonfinite, nc, a0);
+                if (fluid) pend = update_site<L, T, EQ, Store<S>::kProject>(P, g, x, y, t, nonfinite, nc, a0);
             } else {
-                if (fluid) pend = update_site<L, T, EQ>(P, g, x, y, t, nonfinite, nc);
+                if (fluid) pend = update_site<L, T, EQ, Store<S>::kProject>(P, g, x, y, t, nonfinite, nc);
             }
             if (inside) {
 #pragma unroll
-                for (int i = 0; i < L::Q; i++) Store<S>::store(dst + i * plane + o, 0, g[i]);
+                for (int i = 0; i < L::Q; i++)
+                    Store<S>::store(dst + i * plane + o, 0, fluid ? store_round<L, S>(i, g[i]) : g[i]);
             }
         }
         warp_pend(P, pend_list, npend, pend, (unsigned)(y * P.nx + x));
@@ -1121,7 +1274,7 @@ __device__ __forceinline__ void tma_tile(const Params& P, const S* box, int x0, 
                        y0 + R <= P.ny - 1 &&
                        (P.ow == 0 || x0 + TX + 1 <= P.ox0 || x0 - 1 >= P.ox0 + P.ow ||
                         y0 + R + 1 <= P.oy0 || y0 - 1 >= P.oy0 + P.oh);
-    const S* sb = box + (warp + 1) * LY::W + LY::H;
+    const S* sb = box + warp * LY::W + LY::H;
     // Interior tile without the probe site (almost every tile): every site is
     // fluid and away from every boundary rule, so the sites take the shifted
     // shared-memory reads with no per-site checks (the branch is uniform).
@@ -1135,18 +1288,18 @@ __device__ __forceinline__ void tma_tile(const Params& P, const S* box, int x0, 
             const int c = lane + 32 * s;
             T g[L::Q];
 #pragma unroll
-            for (int i = 0; i < L::Q; i++)
-                g[i] = Store<S>::load(sb + i * LY::PLANE + c - L::cx(i) - L::cy(i) * LY::W, 0);
+            for (int i = 0; i < L::Q; i++) g[i] = Store<S>::load(sb + i * LY::PLANE + c - L::cx(i), 0);
             bool pend;
             if constexpr (EQ == EQ_ENERGY_MLP) {
                 float a0[3];
                 mlp_site_start<T>(P, mslot.s, true, g, a0);
-                pend = update_site<L, T, EQ, false>(P, g, x0 + c, y, t, nonfinite, nc, a0);
+                pend = update_site<L, T, EQ, Store<S>::kProject, false>(P, g, x0 + c, y, t, nonfinite, nc, a0);
             } else {
-                pend = update_site<L, T, EQ, false>(P, g, x0 + c, y, t, nonfinite, nc);
+                pend = update_site<L, T, EQ, Store<S>::kProject, false>(P, g, x0 + c, y, t, nonfinite, nc);
             }
 #pragma unroll
-            for (int i = 0; i < L::Q; i++) Store<S>::store(dst + i * plane + row + c, 0, g[i]);
+            for (int i = 0; i < L::Q; i++)
+                Store<S>::store(dst + i * plane + row + c, 0, store_round<L, S>(i, g[i]));
             warp_pend(P, pend_list, npend, pend, site0 + (unsigned)c);
         }
         return;
@@ -1180,6 +1333,7 @@ __global__ void __launch_bounds__(32 * R, tma_min_blocks<S, R, TX>())
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         sh.npend = 0;
         sh.abort = 0;
+        sh.bc.n = 0;
     }
     mslot.fill(P);
     __syncthreads();
@@ -1188,28 +1342,33 @@ __global__ void __launch_bounds__(32 * R, tma_min_blocks<S, R, TX>())
     const int tiles = tiles_x * ((P.ny + R - 1) / R);
 
     // Tiles are handed out in row-major order by a global counter: thread 0
-    // claims one whenever it refills a stage and publishes its index with the
-    // stage's mbarrier (-1: none left; the phase is then completed by a plain
-    // arrive, without a copy).
+    // refills a stage with the tile it claimed at the previous refill and
+    // claims the next one (the atomic's latency then overlaps a tile's
+    // computation), and publishes the tile's index with the stage's mbarrier
+    // (-1: none left; the phase is then completed by a plain arrive, without
+    // a copy).
+    int next_tile = 0;
     auto fill = [&](int st) {
         unsigned long long* bar = &full[st];
-        const int tile = (int)atomicAdd(P.tile_counter, 1u);
+        const int tile = next_tile;
         if (tile >= tiles) {
             sh.tile[st] = -1;
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
             return;
         }
+        next_tile = (int)atomicAdd(P.tile_counter, 1u);
         sh.tile[st] = tile;
         const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
         mbar_expect_tx(bar, (unsigned)LY::TX_BYTES);
         S* base = stages + (size_t)st * (LY::STAGE_BYTES / sizeof(S));
 #pragma unroll
         for (int i = 0; i < L::Q; i++)
-            tma_load_3d(base + i * LY::PLANE, &tm, tx * TX - LY::H, ty * R - 1, i, bar);
+            tma_load_3d(base + i * LY::PLANE, &tm, tx * TX - LY::H, ty * R - L::cy(i), i, bar);
     };
     if (threadIdx.x == 0) {
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<unsigned long long>(&tm))
                      : "memory");
+        next_tile = (int)atomicAdd(P.tile_counter, 1u);
         for (int st = 0; st < STAGES - 1; st++) fill(st);
     }
     bool nonfinite = false;
@@ -1227,29 +1386,30 @@ __global__ void __launch_bounds__(32 * R, tma_min_blocks<S, R, TX>())
             }
             break;
         }
+        // resolve the block's pending sites once its list could not take
+        // another tile's, so that none overflow to the global list (which the
+        // last block alone would resolve).  npend is read after the barrier
+        // above, with no writes to it until the next tile: the branch is
+        // uniform.
+        if (sh.npend > (unsigned)(kPend - TX * R)) {
+            resolve_list<L, S, EQ>(P, (int)min(sh.npend, (unsigned)kPend),
+                                   [&](int j) { return sh.pend[j]; }, &sh.bc, &sh.ss.sc);
+            __syncthreads();
+            if (threadIdx.x == 0) sh.npend = 0;
+            __syncthreads();
+        }
         const int tile = sh.tile[st];
         if (tile < 0) break;
         if (threadIdx.x == 0) {
             // the stage being refilled was last read in iteration jj - 1,
-            // whose reads the barrier at its end ordered before this point
+            // whose reads the barrier at the top of this iteration ordered
+            // before this point
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             fill((jj + STAGES - 1) % STAGES);
         }
         const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
         const S* box = stages + (size_t)st * (LY::STAGE_BYTES / sizeof(S));
         tma_tile<S, EQ, R, TX>(P, box, tx * TX, ty * R, t, sh.pend, &sh.npend, mslot, nonfinite, nc);
-        __syncthreads();
-        // resolve the block's pending sites once its list could not take
-        // another tile's, so that none overflow to the global list (which the
-        // last block alone would resolve).  npend is read between two
-        // barriers with no writes to it in between: the branch is uniform.
-        if (sh.npend > (unsigned)(kPend - TX * R)) {
-            resolve_list<L, S, EQ>(P, (int)min(sh.npend, (unsigned)kPend),
-                                   [&](int j) { return sh.pend[j]; });
-            __syncthreads();
-            if (threadIdx.x == 0) sh.npend = 0;
-            __syncthreads();
-        }
     }
     __syncthreads();
     if (sh.abort && threadIdx.x == 0) {
@@ -1267,7 +1427,7 @@ __global__ void __launch_bounds__(32 * R, tma_min_blocks<S, R, TX>())
     const int scap = (int)min((size_t)kStage, (size_t)STAGES * LY::STAGE_BYTES / 12);
     unsigned long long* skey = reinterpret_cast<unsigned long long*>(smem);
     unsigned* sidx = reinterpret_cast<unsigned*>(smem + 8 * scap);
-    finish_parts<L, S, EQ>(P, sh.pend, sh.npend, sh.is_last, sh.ss, skey, sidx, scap);
+    finish_parts<L, S, EQ>(P, sh.pend, sh.npend, sh.is_last, sh.ss, sh.bc, skey, sidx, scap);
 }
 
 // ---------------------------------------------------------------------------
@@ -1277,7 +1437,10 @@ template <typename L, typename S, int EQ>
 __global__ void __launch_bounds__(kSiteBlock) k_collide_site(const __grid_constant__ Params P) {
     using T = typename Store<S>::T;
     __shared__ FinishShared fs;
-    if (threadIdx.x == 0) fs.npend = 0;
+    if (threadIdx.x == 0) {
+        fs.npend = 0;
+        fs.bc.n = 0;
+    }
     __syncthreads();
     const long long t = *P.step;
     const long long sid = (long long)blockIdx.x * kSiteBlock + threadIdx.x;
@@ -1289,12 +1452,13 @@ __global__ void __launch_bounds__(kSiteBlock) k_collide_site(const __grid_consta
     T g[L::Q];
     if (valid) {
         gather_site<L, S>(P, x, y, g);
-        pending = update_site<L, T, EQ>(P, g, x, y, t, nonfinite, nc);
+        pending = update_site<L, T, EQ, Store<S>::kProject>(P, g, x, y, t, nonfinite, nc);
     }
     if (inside) {
         const long long o = (long long)y * P.nxp + x;
 #pragma unroll
-        for (int i = 0; i < L::Q; i++) Store<S>::store(P.dst, i * P.plane + o, valid ? g[i] : T(0));
+        for (int i = 0; i < L::Q; i++)
+            Store<S>::store(P.dst, i * P.plane + o, valid ? store_round<L, S>(i, g[i]) : T(0));
     }
     warp_pend(P, fs, pending, (unsigned)sid);
     if (nonfinite) atomicOr(P.err, ERR_NONFINITE);
@@ -1311,13 +1475,24 @@ __global__ void __launch_bounds__(kSelectThreads) k_select(const __grid_constant
 }
 
 #ifdef LBM_DEFINE_EMIT_FROM_DS
-// Candidates from a given dS array (select-only test hook): the same warp
-// append as K1.
+// Candidates from a given dS array (select-only test hook): each block of
+// 256 threads takes kEmitPerBlock consecutive values through the same block
+// stage as K1 (its k best reach the global list).
+constexpr int kEmitPerBlock = 2048;
 __global__ void __launch_bounds__(256) k_emit_from_ds(const __grid_constant__ Params P, const double* ds,
                                                       int n) {
-    const long long i = (long long)blockIdx.x * 256 + threadIdx.x;
-    const double v = i < n ? ds[i] : -INFINITY;
-    if (P.k > 0) warp_push<double>(P, i < n && v > P.delta, v, (unsigned)i);
+    __shared__ BlockCand bc;
+    __shared__ TopkScratch sc;
+    if (threadIdx.x == 0) bc.n = 0;
+    if (P.k <= 0) return;
+    const long long b0 = (long long)blockIdx.x * kEmitPerBlock;
+    for (int r = 0; r < kEmitPerBlock; r += 256) {
+        block_room(P, bc, sc);
+        const long long i = b0 + r + threadIdx.x;
+        const double v = i < n ? ds[i] : -INFINITY;
+        block_push<double>(P, bc, i < n && v > P.delta, v, (unsigned)i);
+    }
+    block_finish(P, bc, sc);
 }
 #endif
 
@@ -1339,17 +1514,22 @@ __global__ void k_init_eq(const __grid_constant__ Params P, const double* rho, c
 #pragma unroll
         for (int i = 0; i < L::Q; i++) gs[i] = T(0);
     } else {
-        const T r = T(rho[sid]), u = T(ux[sid]), v = uy ? T(uy[sid]) : T(0);
+        const double v = uy ? uy[sid] : 0.0;
+        bool done = false;
         if constexpr (EQ >= EQ_ENERGY) {
             if (e2) {
+                const T r = T(rho[sid]), u = T(ux[sid]);
                 NewtonCount nc = {0, 0, 0, 0};
-                equilibrium_energy<T, EQ>(P, r, r * u, r * v, T(e2[sid]), gs, nc);
-            } else {
-                feq_entropic<L, T>(r, u, v, Par<T>::rho0(P), gs);   // isothermal energy
+                equilibrium_energy<T, EQ>(P, r, r * u, r * T(v), T(e2[sid]), gs, nc);
+#pragma unroll
+                for (int i = 0; i < L::Q; i++) gs[i] = store_round<L, S>(i, gs[i]);
+                done = true;
             }
-        } else {
-            equilibrium<L, T, EQ>(P, r - Par<T>::rho0(P), r, u, v, gs);
         }
+        // polynomial or entropic f* (the energy forms without a given energy:
+        // the isothermal entropic formula) in FP64, held as the storage
+        // holds it
+        if (!done) bc_equilibrium<L, S>(P, rho[sid], ux[sid], v, gs);
     }
 #pragma unroll
     for (int i = 0; i < L::Q; i++) Store<S>::store(P.dst, i * P.plane + o, gs[i]);
@@ -1364,18 +1544,17 @@ __global__ void k_import(const __grid_constant__ Params P, const double* f) {
     const int x = (int)(sid % P.nx), y = (int)(sid / P.nx);
     const long long o = (long long)y * P.nxp + x;
     const bool solid = is_solid(P, x, y);
+    using T = typename Store<S>::T;
     if (P.rho0 == 0.0) {
-        // plain storage: a conversion only (no FP64 arithmetic)
+        // FP64 storage: a copy (no FP64 arithmetic)
 #pragma unroll
         for (int i = 0; i < L::Q; i++)
-            Store<S>::store(P.dst, i * P.plane + o, (typename Store<S>::T)(solid ? 0.0 : f[i * N + sid]));
+            Store<S>::store(P.dst, i * P.plane + o, (T)(solid ? 0.0 : f[i * N + sid]));
         return;
     }
 #pragma unroll
-    for (int i = 0; i < L::Q; i++) {
-        const double v = solid ? 0.0 : f[i * N + sid] - L::w(i) * P.rho0;
-        Store<S>::store(P.dst, i * P.plane + o, (typename Store<S>::T)v);
-    }
+    for (int i = 0; i < L::Q; i++)
+        Store<S>::store(P.dst, i * P.plane + o, solid ? T(0) : dev_of_f64<L, S>(P, i, f[i * N + sid]));
 }
 
 // Pre-collision state of the current step (gather of src), exported as
@@ -1403,7 +1582,7 @@ __global__ void k_export(const __grid_constant__ Params P, int mode, double* o0,
     gather_site<L, S>(P, x, y, g);
     if (mode == 0) {
 #pragma unroll
-        for (int i = 0; i < L::Q; i++) o0[i * N + sid] = (double)g[i] + L::w(i) * P.rho0;
+        for (int i = 0; i < L::Q; i++) o0[i * N + sid] = pop_f64<L, S>(P, i, g[i]);
     } else if (mode == 1) {
         if constexpr (sizeof(T) == 4) {
             // FP32 / FP16 storage: the sums of the stored values in float-float
@@ -1423,8 +1602,21 @@ __global__ void k_export(const __grid_constant__ Params P, int mode, double* o0,
                 const int c2 = L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i);
                 if (c2 > 0) e = ff_add(e, ff_scale(gi, (float)c2));
             }
-            const double rho = (P.rho0 + (double)r.hi) + (double)r.lo;
-            const ff rf = ff_add({P.rho0f, 0.0f}, r);
+            // the stored deviations' offsets: sum W rho0 (= rho0), and for
+            // plain FP32 the sums of the FP32 weights (exact in FP64)
+            double off0 = P.rho0, off2 = L::sum_w_c2 * P.rho0;
+            if constexpr (Store<S>::kPlain) {
+                off0 = 0.0;
+                off2 = 0.0;
+#pragma unroll
+                for (int i = 0; i < L::Q; i++) {
+                    off0 += (double)(float)L::w(i);
+                    off2 += (double)(L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i)) * (double)(float)L::w(i);
+                }
+            }
+            const double rho = (off0 + (double)r.hi) + (double)r.lo;
+            const float o0h = (float)off0;
+            const ff rf = ff_add({o0h, (float)(off0 - (double)o0h)}, r);
             const ff ir = ff_recip(rf);
             o0[sid] = rho;
             if (o1) {
@@ -1435,7 +1627,7 @@ __global__ void k_export(const __grid_constant__ Params P, int mode, double* o0,
                 const ff v = ff_mul(jy, ir);
                 o2[sid] = (double)v.hi + (double)v.lo;
             }
-            if (o3) o3[sid] = (L::sum_w_c2 * P.rho0 + (double)e.hi) + (double)e.lo;
+            if (o3) o3[sid] = (off2 + (double)e.hi) + (double)e.lo;
         } else {
             double rho = 0, jx = 0, jy = 0, e2 = 0;
 #pragma unroll

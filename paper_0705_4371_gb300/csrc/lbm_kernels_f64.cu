@@ -11,7 +11,7 @@ Launchers launchers_f64(int lattice, int eq) {
 
 namespace lbm {
 cudaError_t launch_emit_from_ds(const Params& P, const double* ds, int n, cudaStream_t st) {
-    const unsigned blocks = (unsigned)((n + 255) / 256);
+    const unsigned blocks = (unsigned)((n + kEmitPerBlock - 1) / kEmitPerBlock);
     k_emit_from_ds<<<blocks > 0 ? blocks : 1, 256, 0, st>>>(P, ds, n);
     return cudaGetLastError();
 }

@@ -40,7 +40,7 @@ def test_elbm_shock_tube_matches_oracle(lbm, nu, reg):
     assert e_rho < 1e-12 and e_u < 1e-12
 
 
-@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 5e-5)])
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 1e-5)])
 def test_elbm_cylinder_matches_oracle(lbm, prec, tol):
     w = inputs.cylinder(200, 72, 8, 5000.0, delta=1e-5, k=16, eq=inputs.EQ_ENTROPIC)
     cfg = oracle_cfg(w, elbm=True)

@@ -170,9 +170,7 @@ def test_full_size_c5_batch_runs_match_the_oracle(lbm, variant):
 def test_full_size_precision_form_error_table(lbm):
     # the precision form at its own size: the 4096 x 2048 cylinder at Re 20000
     # for 1000 steps from the seeded inflow (noise 1e-4); every storage replays
-    # the FP64 GPU run's selections; moment errors against that run.  The
-    # unstable shear layers of Re 20000 amplify rounding over the run, so
-    # the bounds here are looser than the Re 1000 ones of the small grid.
+    # the FP64 GPU run's selections; moment errors against that run.
     w = inputs.workload_c3()
     rho, ux, uy = inputs.cylinder_fields(w)
     ref = lbm.Lattice.from_workload(w, precision=lbm.LB_F64)
@@ -194,25 +192,75 @@ def test_full_size_precision_form_error_table(lbm):
         out[prec] = moment_errors((r, u, v), (r64, u64, v64), m, w.u_in[0])
         print("4096 x 2048, 1000 steps, %s vs FP64 GPU: M %.3g rho %.3g u %.3g" % ((prec,) + out[prec]))
     assert sum(len(s) for s in sels) > 0
-    assert out["f32dev"][0] < 1e-4 and out["f32"][0] < 1e-3 and out["f16dev"][0] < 3e-2
+    assert out["f32dev"][0] < 1e-5 and out["f32"][0] < 1e-5 and out["f16dev"][0] < 3e-2
     assert out["f32dev"][0] <= out["f32"][0]     # deviation storage is the more accurate
 
 
-@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32dev", 1e-4), ("f32", 1e-3), ("f16dev", 3e-2)])
-def test_scaled_precision_workload_vs_the_oracle(lbm, prec, tol):
-    # the same layout at 1/8 scale (512 x 256, L = 16, Re 20000) against the
-    # FP64 oracle, 1000 steps with the oracle's selections replayed
+@pytest.mark.parametrize("prec", ["f64", "f32dev", "f32", "f16dev"])
+def test_scaled_precision_workload_vs_the_oracle(lbm, prec):
+    # the same layout at 1/8 scale (512 x 256, L = 16, Re 20000, inflow
+    # noise 1e-4) against the FP64 oracle, 1000 steps with the oracle's
+    # selections replayed.  This wake amplifies any perturbation: the oracle
+    # itself, run with the storage's rounding (exact arithmetic), is already
+    # 1.5e-6 (FP32 deviation) / 4.9e-6 (plain FP32) off in M and 2.5e-5 /
+    # 9.7e-5 in u.  The GPU is held to a small multiple of that floor, and
+    # FP32 deviation storage to the 1e-5 target in M.
+    from tests.test_gpu_precision import STORE, stored
     w = inputs.workload_c3_scaled()
     cfg = oracle_cfg(w)
     rho, ux, uy = inputs.cylinder_fields(w)
-    fo, log = ora.run(cfg, ora.init_field(cfg, rho, ux, uy), 1000)
+    f0 = ora.init_field(cfg, rho, ux, uy)
+    fo, log = ora.run(cfg, f0.copy(), 1000)
     ro, uo, vo, _ = ora.moment_fields(cfg, fo)
+    mask = cfg.solid_mask()
     with lbm.Lattice.from_workload(w, precision=lbm.PRECISIONS[prec]) as g:
         g.init_equilibrium(rho, ux, uy)
         g.replay_selection(log.selected)
         g.step(1000)
         r, u, v, _ = g.moments()
-    e = moment_errors((r, u, v), (ro, uo, vo), cfg.solid_mask(), w.u_in[0])
-    print("512 x 256, 1000 steps, %s vs oracle: M %.3g rho %.3g u %.3g (Ehrenfests' sites %d)"
-          % ((prec,) + e + (int(log.counts.sum()),)))
-    assert e[0] < tol and e[1] < tol
+    e = moment_errors((r, u, v), (ro, uo, vo), mask, w.u_in[0])
+    if prec == "f64":
+        floor = (0.0, 0.0, 0.0)
+        assert e[0] < 1e-12 and e[1] < 1e-12
+    else:
+        cf = oracle_cfg(w, store=STORE[prec])
+        ff, _ = ora.run(cf, stored(f0, STORE[prec]), 1000, replay=log.selected)
+        floor = moment_errors(ora.moment_fields(cf, ff)[:3], (ro, uo, vo), mask, w.u_in[0])
+        for c in range(3):
+            assert e[c] <= 6.0 * floor[c] + 2e-7, (c, e[c], floor[c])
+        if prec == "f32dev":
+            assert e[0] < 1e-5 and e[1] < 1e-5
+    print("512 x 256, 1000 steps, %s vs oracle: M %.3g rho %.3g u %.3g | storage floor M %.3g rho %.3g u %.3g"
+          " (Ehrenfests' sites %d)" % ((prec,) + e + floor + (int(log.counts.sum()),)))
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_full_size_every_site_a_candidate_selects_like_the_oracle(lbm, prec):
+    # delta < 0: every fluid site is a candidate (dS >= 0 > delta).  Each
+    # block keeps its k = 16 best, so the global select ranks at most
+    # 16 x blocks keys instead of all 8.4 M.  The selection equals the
+    # oracle's on the same dS array (the run's exact dS of the state,
+    # exported), on the first step after a state upload (every tile through
+    # the general gather) and on the next (the interior fast path).
+    w = inputs.workload_c3()
+    g = _spun_up(lbm, w, prec)
+    f0 = g.get_state()
+    g.close()
+    w.delta, w.k = -1.0, 16
+    h = lbm.Lattice.from_workload(w, precision=lbm.PRECISIONS[prec])
+    h.set_state(f0)
+    eligible = ~w.solid_mask().ravel()
+    for step in range(3):
+        ds = h.delta_s().ravel()
+        assert np.isfinite(ds[eligible]).all()
+        h.step(1)
+        want = ora.select(np.where(eligible, ds, -np.inf), w.delta, w.k)
+        assert np.array_equal(h.selected(), want), step
+    assert (h.counts(3) == w.k).all()
+    # step time with every site a candidate, beside the plain step's
+    h.set_timing(True)
+    h.step(10)
+    h.sync()
+    t = h.kernel_times(reset=True)
+    print("every site a candidate (%s): %.3f ms per step" % (prec, t["collide_ms"] / t["collide_launches"]))
+    h.close()
