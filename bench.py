@@ -3,10 +3,13 @@ replicas), printed as one JSON line.
 
 Workload (default): square cylinder of side L = 128 in a 4096 x 2048
 free-slip channel, Re = 20000, inflow u = 0.05 with seeded 1e-4 noise,
-polynomial equilibrium, delta = 1e-3, k = 16, populations stored in plain
-FP32.  One bench step = one lattice time step of the whole hot path:
-pull-stream + collide + dS + block top-k (one kernel) and global select +
-Ehrenfests' step (one single-block kernel).
+polynomial equilibrium, delta = 1e-3, k = 16, populations stored as FP32
+deviations f - W_i rho0 (the precision workload's storage).  One bench step
+= one lattice time step of the whole hot path in one launch: pull-stream +
+collide + dS + each block's k best candidates, then, in the launch's last
+block, the global select + Ehrenfests' step.  The forms beside it: plain
+FP32 and FP16 deviation storage on the same grid, every site a candidate
+(delta < 0), the 600 x 500 channel, the learned and the batched forms.
 
   python bench.py [--steps K] [--warmup W] [--precision f32|f32dev|f16dev|f64]
   python bench.py --impl reference     # the FP64 CPU oracle as the reference arm
@@ -287,6 +290,7 @@ def run_gpu(args):
                                 "bytes_per_site": inf2["bytes_per_site"]}
 
     if args.forms and rank == 0:
+        forms["select_stress"] = select_stress_form(args, stream, w)
         forms["c2"] = c2_form(args, stream)
     if args.forms and args.learned and rank == 0:
         forms["learned"] = learned_form(args, stream)
@@ -328,6 +332,38 @@ def run_gpu(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def select_stress_form(args, stream, w):
+    """The headline workload with delta < 0: every fluid site is a candidate
+    (dS >= 0 > delta), each block keeps its k = 16 best and the last block
+    ranks at most k x blocks of them.  Step time over 20 steps after the
+    same spin-up, beside the headline's."""
+    import torch
+    from paper_0705_4371_gb300 import lbm
+    from copy import copy
+    ws = copy(w)
+    ws.delta = -1.0
+    with lbm.Lattice.from_workload(ws, precision=lbm.PRECISIONS[args.precision],
+                                   stream=stream.cuda_stream) as h2:
+        h2.init_equilibrium(*inputs.cylinder_fields(ws))
+        h2.step(args.spinup)
+        h2.set_timing(True)
+        h2.step(3)
+        h2.sync()
+        h2.kernel_times(reset=True)
+        n = 20
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h2.step(n)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        counts = h2.counts(n)
+    return {"delta": -1.0, "k": ws.k, "ms_per_step": round(ms / n, 4),
+            "MLUPS": round(ws.n_sites * n / (ms * 1e-3) / 1e6, 1),
+            "sites_per_step": int(counts.max()), "steps": n,
+            "note": "every fluid site's exact dS evaluated and ranked each step"}
 
 
 def c2_form(args, stream):

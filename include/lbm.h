@@ -333,16 +333,71 @@ int lb_kernel_times(lb_handle* h, double* collide_ms, long long* collide_launche
 /* Tile shape of the D2Q9 stream-collide kernel.  Register-fed shapes (sites
  * per thread in x, warps per block, minimum resident blocks per SM):
  * 0 = 1, 8, 3;  1 = 1, 8, 4;  2 = 2, 8, 2;  3 = 4, 8, 1.
- * Shared-memory-staged shapes (tensor-memory-accelerator copies of the
- * R x C-site block tile of every population plane plus one halo row and
- * 16 bytes of halo columns; R rows, C columns, STAGES tiles in flight per
- * block): 4 = 8 x 128, STAGES 2 (default);  5 = 4 x 128, STAGES 3;
- * 6 = 8 x 64, STAGES 2 (three blocks per SM).  The energy-constrained forms
- * are built for shapes 0 (1, 8, 2: 128 registers per thread), 1 (2 and 3
- * run 1) and 4 (5 and 6 run 4); their defaults: 1 for FP64 storage, 4 for
- * the Newton start and 0 for the network's warm start in FP32 / FP16
- * storage.  Results do not depend on the shape; only the speed does. */
+ * Shared-memory-staged shapes (tensor-memory-accelerator copies, for every
+ * population plane, of the R rows of the R x C-site block tile's sources in
+ * that plane plus 16 bytes of halo columns; R rows, C columns, STAGES tiles
+ * in flight per block): 4 = 8 x 128, STAGES 2 (default of FP64 and FP16
+ * storage);  5 = 6 x 128, STAGES 3 (default of FP32 storage, plain and
+ * deviation);  6 = 8 x 64, STAGES 2 (three blocks per SM).  The
+ * energy-constrained forms are built for shapes 0 (1, 8, 2: 128 registers
+ * per thread), 1 (2 and 3 run 1), 4 and 5, and refuse 6 (LB_ERR_ARG); their
+ * defaults: 1 for FP64 storage, 4 for the Newton start and 0 for the
+ * network's warm start in FP32 / FP16 storage.  Results do not depend on
+ * the shape; only the speed does. */
 int lb_set_tile_shape(lb_handle* h, int shape);
+
+/* ------------------------------------------------------------------------
+ * One run sharded in x over several handles (one per GPU): each handle holds
+ * a slab of columns plus one ghost column on every side that faces another
+ * slab.  The selection of Sec. 3.2 is global -- the k sites of the whole
+ * grid with the largest dS > delta -- so each step is:
+ *   lb_slab_collide     stream + collide of the slab (ghost columns hold the
+ *                       neighbours' post-collision populations of the
+ *                       previous step), ending with the slab's own k best
+ *                       candidates;
+ *   lb_slab_candidates  those candidates (key, global site index) to the
+ *                       host; the caller gathers every slab's and keeps the
+ *                       k best of the union (key descending, global index
+ *                       ascending) -- the same set one unsharded run selects;
+ *   lb_slab_apply       that global selection: the Ehrenfests' step at the
+ *                       slab's own selected sites; completes the step;
+ *   lb_slab_ghost       pack the populations leaving through a face into a
+ *                       device buffer / unpack the neighbour's into the ghost
+ *                       column, before the next lb_slab_collide.
+ * lb_step is refused on a slab.  D2Q9 only.
+ * ------------------------------------------------------------------------ */
+
+/* Make h (created with the slab's local grid: its nx counts the ghost
+ * columns; boundary kinds of the global run on its outer sides, any
+ * non-periodic kind on a side facing another slab; obstacle in local
+ * coordinates) a slab.  ghost_left / ghost_right: 1 where another slab lies
+ * on that side, else 0; global_x0: global x of the slab's first own column;
+ * global_nx: columns of the whole grid.  A slab owns at least three columns.
+ * Allocates the slab's candidate and selection lists (device). */
+int lb_set_slab(lb_handle* h, int ghost_left, int ghost_right, int global_x0, int global_nx);
+
+/* Queue the slab's stream + collide launch (asynchronous); its last block
+ * keeps the slab's k best candidates instead of applying them. */
+int lb_slab_collide(lb_handle* h);
+
+/* The slab's candidates of the collided step (synchronises): keys (host,
+ * monotone uint64 images of dS, larger = larger dS) and global site indices
+ * (y * global_nx + x), at most cap of them; *count = how many (<= k). */
+int lb_slab_candidates(lb_handle* h, unsigned long long* keys, long long* global_idx, int cap, int* count);
+
+/* Apply the step's global selection (m host global site indices, any
+ * order, m <= k): f' <- f* at the slab's own sites among them (Sec. 3.2;
+ * (ESLB)); logs the slab's share of the count; completes the step
+ * (synchronises). */
+int lb_slab_apply(lb_handle* h, const long long* global_idx, int m);
+
+/* Ghost exchange of the completed step (asynchronous on the run's stream):
+ * direction 0 packs the three populations that leave through side (0 left,
+ * 1 right) -- those moving toward that neighbour, of the slab's first or
+ * last own column -- into buf; direction 1 writes buf into the ghost column
+ * on that side.  buf: DEVICE array of 3 * ny values of the storage type
+ * (planes 3, 6, 7 or 1, 5, 8, each [ny]), owned by the caller. */
+int lb_slab_ghost(lb_handle* h, int side, void* buf, int direction);
 
 /* Run facts (out: 8 entries): out[0] = Q, out[1] = padded row length
  * (elements), out[2] = bytes per stored population, out[3] = algorithmic

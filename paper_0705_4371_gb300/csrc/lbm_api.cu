@@ -44,15 +44,18 @@ int fail(int code, const char* fmt, ...) {
 
 constexpr int kGraphSteps = 32;      // steps per captured graph (even: buffers return)
 constexpr int kDefaultLog = 65536;
-constexpr int kDefaultTileShape = 4;  // fastest measured on GB300 (staged tiles, 2 in flight)
-// The energy forms are bound by the Newton solve, not by memory (fastest
-// measured on GB300): FP64 storage's FP64 finish wants the most resident warps
+// Default tile shapes, the fastest measured on GB300: FP32 storage (plain
+// and deviation) stages 6-row tiles with 2 more in flight per block (shape
+// 5); FP16 and FP64 storage 8-row tiles with 1 more (shape 4; FP16 with
+// three blocks per SM).  The energy forms are bound by the Newton solve, not
+// by memory: FP64 storage's FP64 finish wants the most resident warps
 // (register-fed shape 1); the float-float finish of FP32 / FP16 storage runs
-// best in the staged shape, and the network's warm start in the register-fed
-// shape with 128 registers (shape 0), where its fragments spill least.
+// best in the staged shape 4, and the network's warm start in the
+// register-fed shape with 128 registers (shape 0), where its fragments spill
+// least.
 int default_tile_shape(int lattice, int eq, int precision) {
     if (lattice != LB_D2Q9) return 0;
-    if (eq < LB_EQ_ENTROPIC_ENERGY) return kDefaultTileShape;
+    if (eq < LB_EQ_ENTROPIC_ENERGY) return (precision == LB_F32 || precision == LB_F32_DEV) ? 5 : 4;
     if (precision == LB_F64) return 1;
     return eq == LB_EQ_ENTROPIC_ENERGY_MLP ? 0 : 4;
 }
@@ -141,6 +144,15 @@ struct lb_handle {
     // tensor maps of the two population buffers (shared-memory-staged shapes)
     CUtensorMap tmap[2];
     unsigned* tile_counter;
+    // slab of a run sharded in x: ghost columns on each side, global x of the
+    // first owned column, global nx; the keys of the slab's best candidates;
+    // the step's selection among the slab's sites (one replayed step)
+    int slab, ghost_l, ghost_r, gx0, gnx;
+    bool slab_collided;
+    unsigned long long* sel_key;
+    int* slab_sel;
+    int* slab_cnt;
+    long long* slab_off;
 };
 
 namespace {
@@ -200,6 +212,10 @@ Params make_params(const lb_handle* h, int src, bool prestream) {
     P.tile_counter = h->tile_counter;
     P.elbm = h->elbm ? 1 : 0;
     P.wall = h->bc.obstacle_wall;
+    P.slab = h->slab;
+    P.own_x0 = h->slab ? h->ghost_l : 0;
+    P.own_x1 = h->slab ? h->nx - h->ghost_r : h->nx;
+    P.sel_key = h->slab ? h->sel_key : nullptr;
     return P;
 }
 
@@ -397,7 +413,8 @@ void lb_destroy(lb_handle* h) {
     void* ptrs[] = {h->buf[0], h->buf[1], h->cand_key, h->cand_idx, h->cand_count, h->sel_idx,
                     h->sel_count, h->count_ring, h->probe_ring, h->d_step, h->d_err, h->replay_cnt,
                     h->replay_off, h->replay_idx, h->mlp, h->newton_stats, h->ticket,
-                    h->pend_idx, h->pend_count, h->tile_counter, h->stage};
+                    h->pend_idx, h->pend_count, h->tile_counter, h->stage, h->sel_key, h->slab_sel,
+                    h->slab_cnt, h->slab_off};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_err) cudaFreeHost(h->h_err);
@@ -645,6 +662,7 @@ int lb_delta_s(lb_handle* h, double* ds, int on_device) {
 int lb_step(lb_handle* h, int n) {
     if (!h) return fail(LB_ERR_ARG, "NULL handle");
     if (n < 0) return fail(LB_ERR_ARG, "n must be >= 0");
+    if (h->slab) return fail(LB_ERR_STATE, "a slab steps with lb_slab_collide and lb_slab_apply");
     int rc = check_sticky(h, false);
     if (rc != LB_OK) return rc;
     if (h->eq == LB_EQ_ENTROPIC_ENERGY_MLP && !h->mlp_set)
@@ -914,12 +932,136 @@ int lb_set_tile_shape(lb_handle* h, int shape) {
     if (!h) return fail(LB_ERR_ARG, "NULL handle");
     if (shape < 0 || shape >= kTileShapes) return fail(LB_ERR_ARG, "tile shape must be in [0, %d)", kTileShapes);
     if (h->lattice != LB_D2Q9) return fail(LB_ERR_ARG, "tile shapes apply to D2Q9 runs");
+    if (shape == 6 && h->eq >= LB_EQ_ENTROPIC_ENERGY)
+        return fail(LB_ERR_ARG, "the energy forms take tile shapes 0-5");
     CK(cudaStreamSynchronize(h->stream));
     h->tile_shape = shape;
     drop_graphs(h);
     const int rc = size_grid(h);
     if (rc != LB_OK) return rc;
     return make_tensor_maps(h);
+}
+
+// ---------------------------------------------------------------------------
+// Slabs of a run sharded in x (the selection of Sec. 3.2 is global: the k
+// sites with the largest dS of the whole grid).
+// ---------------------------------------------------------------------------
+
+int lb_set_slab(lb_handle* h, int ghost_left, int ghost_right, int global_x0, int global_nx) {
+    if (!h) return fail(LB_ERR_ARG, "NULL handle");
+    if (h->lattice != LB_D2Q9) return fail(LB_ERR_ARG, "slabs are built for D2Q9");
+    if (h->slab) return fail(LB_ERR_STATE, "the handle is already a slab");
+    if ((ghost_left != 0 && ghost_left != 1) || (ghost_right != 0 && ghost_right != 1))
+        return fail(LB_ERR_ARG, "a slab has at most one ghost column on each side");
+    const int own = h->nx - ghost_left - ghost_right;
+    if (own < 3) return fail(LB_ERR_ARG, "a slab owns at least three columns");
+    if (global_x0 < 0 || global_x0 + own > global_nx) return fail(LB_ERR_ARG, "slab outside the global grid");
+    if ((ghost_left == 0) != (global_x0 == 0) || (ghost_right == 0) != (global_x0 + own == global_nx))
+        return fail(LB_ERR_ARG, "ghost columns on exactly the sides that face another slab");
+    if ((long long)h->ny * global_nx >= (1ll << 31)) return fail(LB_ERR_ARG, "global grid too large");
+    if (h->replay_n > 0) return fail(LB_ERR_STATE, "a slab cannot replay selections");
+    CK(cudaStreamSynchronize(h->stream));
+    const long long cap = std::max(1ll, h->sel_cap);
+    CK(cudaMalloc(&h->sel_key, cap * sizeof(unsigned long long)));
+    CK(cudaMalloc(&h->slab_sel, cap * sizeof(int)));
+    CK(cudaMalloc(&h->slab_cnt, sizeof(int)));
+    CK(cudaMalloc(&h->slab_off, sizeof(long long)));
+    CK(cudaMemset(h->slab_off, 0, sizeof(long long)));
+    h->slab = 1;
+    h->ghost_l = ghost_left;
+    h->ghost_r = ghost_right;
+    h->gx0 = global_x0;
+    h->gnx = global_nx;
+    drop_graphs(h);
+    return LB_OK;
+}
+
+int lb_slab_collide(lb_handle* h) {
+    if (!h) return fail(LB_ERR_ARG, "NULL handle");
+    if (!h->slab) return fail(LB_ERR_STATE, "not a slab (lb_set_slab)");
+    if (h->slab_collided) return fail(LB_ERR_STATE, "the previous step's selection was not applied");
+    int rc = check_sticky(h, false);
+    if (rc != LB_OK) return rc;
+    if (h->eq == LB_EQ_ENTROPIC_ENERGY_MLP && !h->mlp_set)
+        return fail(LB_ERR_STATE, "the learned equilibrium needs its network (lb_set_mlp) first");
+    rc = queue_step(h, h->cur, h->prestream, h->timing);
+    if (rc != LB_OK) return rc;
+    h->slab_collided = true;
+    return LB_OK;
+}
+
+int lb_slab_candidates(lb_handle* h, unsigned long long* keys, long long* global_idx, int cap, int* count) {
+    if (!h || !count || (cap > 0 && (!keys || !global_idx))) return fail(LB_ERR_ARG, "NULL argument");
+    if (!h->slab_collided) return fail(LB_ERR_STATE, "no collided step (lb_slab_collide)");
+    int c = 0;
+    CK(cudaMemcpyAsync(&c, h->sel_count, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    *count = c;
+    const int m = std::min(c, cap);
+    if (m > 0) {
+        std::vector<int> idx(m);
+        CK(cudaMemcpyAsync(idx.data(), h->sel_idx, m * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaMemcpyAsync(keys, h->sel_key, m * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        for (int j = 0; j < m; j++) {
+            const int x = idx[j] % h->nx, y = idx[j] / h->nx;
+            global_idx[j] = (long long)y * h->gnx + (h->gx0 + x - h->ghost_l);
+        }
+    }
+    return check_sticky(h, true);
+}
+
+int lb_slab_apply(lb_handle* h, const long long* global_idx, int m) {
+    if (!h || m < 0 || (m > 0 && !global_idx)) return fail(LB_ERR_ARG, "bad argument");
+    if (!h->slab_collided) return fail(LB_ERR_STATE, "no collided step (lb_slab_collide)");
+    if (m > h->k) return fail(LB_ERR_ARG, "more selected sites (%d) than k (%d)", m, h->k);
+    std::vector<int> own;
+    const int own_w = h->nx - h->ghost_l - h->ghost_r;
+    for (int j = 0; j < m; j++) {
+        const long long g = global_idx[j];
+        if (g < 0 || g >= (long long)h->ny * h->gnx) return fail(LB_ERR_ARG, "site %lld outside the grid", g);
+        const int gx = (int)(g % h->gnx), y = (int)(g / h->gnx);
+        if (gx >= h->gx0 && gx < h->gx0 + own_w) own.push_back(y * h->nx + (gx - h->gx0 + h->ghost_l));
+    }
+    const int c = (int)own.size();
+    CK(cudaMemcpyAsync(h->slab_cnt, &c, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    if (c > 0) CK(cudaMemcpyAsync(h->slab_sel, own.data(), c * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    // the Ehrenfests' step at the slab's selected sites, as one replayed step
+    Params P = make_params(h, h->cur, h->prestream);
+    P.replay_cnt = h->slab_cnt;
+    P.replay_off = h->slab_off;
+    P.replay_idx = h->slab_sel;
+    P.replay_t0 = h->h_step;
+    P.replay_n = 1;
+    CK(h->L.select(P, kSelectStageCap, 0, h->stream));
+    CK(cudaStreamSynchronize(h->stream));   // the host copies of the lists are local
+    h->slab_collided = false;
+    h->prestream = false;
+    h->cur = 1 - h->cur;
+    h->h_step++;
+    return queue_err_readback(h);
+}
+
+int lb_slab_ghost(lb_handle* h, int side, void* buf, int direction) {
+    if (!h || !buf) return fail(LB_ERR_ARG, "NULL argument");
+    if (!h->slab) return fail(LB_ERR_STATE, "not a slab (lb_set_slab)");
+    if (h->slab_collided) return fail(LB_ERR_STATE, "the step's selection was not applied");
+    if (side != 0 && side != 1) return fail(LB_ERR_ARG, "side is 0 (left) or 1 (right)");
+    if (direction != 0 && direction != 1) return fail(LB_ERR_ARG, "direction is 0 (pack) or 1 (unpack)");
+    if ((side == 0 && !h->ghost_l) || (side == 1 && !h->ghost_r)) return fail(LB_ERR_ARG, "no neighbour on that side");
+    // pack: the outgoing populations of the first (left) or last (right)
+    // owned column; unpack: the incoming ones into the ghost column
+    int col, right;
+    if (direction == 0) {
+        col = side == 0 ? h->ghost_l : h->nx - 1 - h->ghost_r;
+        right = side == 1;
+    } else {
+        col = side == 0 ? 0 : h->nx - 1;
+        right = side == 0;
+    }
+    Params P = make_params(h, h->cur, false);
+    CK(h->L.ghost(P, h->buf[h->cur], col, right, buf, direction, h->stream));
+    return LB_OK;
 }
 
 int lb_info(lb_handle* h, long long* out, double* beta_out) {

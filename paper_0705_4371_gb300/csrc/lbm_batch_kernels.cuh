@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(32 * R, 16 / R) k_collide_batch(const __grid_c
         bool nonfinite = false;
         NewtonCount nc = {0, 0, 0, 0};
         const S* box = stages + (size_t)st * (LY::STAGE_BYTES / sizeof(S));
-        tma_tile<S, EQ, R>(P, box, tx * TX, ty * R, t, sh.pend, &sh.npend, mslot, nonfinite, nc);
+        tma_tile<S, EQ, R>(P, box, tx * TX, ty * R, t, sh.pend, &sh.npend, kPend, mslot, nonfinite, nc);
         const int nf = __syncthreads_or(nonfinite);
         // the tile's pending sites (npend is read between barriers: uniform)
         if (sh.npend > 0) {

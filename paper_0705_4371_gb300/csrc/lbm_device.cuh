@@ -85,6 +85,7 @@ struct Params {
     unsigned* cand_count;
     int cand_per_block;
     int* sel_idx;
+    unsigned long long* sel_key;   // keys of the selected candidates (written when not null)
     int* sel_count;
     // logs
     int* count_ring;
@@ -114,6 +115,11 @@ struct Params {
     unsigned* tile_counter;   // next tile to hand out (staged shapes)
     int elbm;                 // ELBM collision (elbmLB) instead of LBGK (entropic f* only)
     int wall;                 // rule on the obstacle's faces: WALL_BOUNCE_BACK / WALL_DIFFUSE
+    // slab of a run sharded in x: only columns [own_x0, own_x1) are the
+    // slab's sites (the others are ghost copies of the neighbours' columns);
+    // the stream-collide launch ends with the slab's own k best candidates
+    // (select only), the global selection being applied afterwards
+    int slab, own_x0, own_x1;
 };
 
 template <int Q, typename T> struct PopArr { T v[Q]; };
@@ -185,8 +191,10 @@ template <> __host__ __device__ __forceinline__ double dfma<double>(double a, do
 // v . u for lattice velocity components in {-1, 0, 1}: additions only.
 template <typename L, typename T>
 __host__ __device__ __forceinline__ T cdotu(int i, T ux, T uy) {
-    const T a = L::cx(i) == 1 ? ux : (L::cx(i) == -1 ? -ux : T(0));
-    const T b = L::cy(i) == 1 ? uy : (L::cy(i) == -1 ? -uy : T(0));
+    const T a = L::cx(i) == 1 ? ux : -ux;
+    const T b = L::cy(i) == 1 ? uy : -uy;
+    if (L::cx(i) == 0) return L::cy(i) == 0 ? T(0) : b;
+    if (L::cy(i) == 0) return a;
     return a + b;
 }
 

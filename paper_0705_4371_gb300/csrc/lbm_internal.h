@@ -20,6 +20,8 @@ struct Launchers {
     cudaError_t (*export_state)(const Params&, int mode, double*, double*, double*, double*,
                                 cudaStream_t);
     cudaError_t (*set_smem)(int stage_cap);
+    // slab ghost exchange: column col of field <-> packed buffer [3][ny]
+    cudaError_t (*ghost)(const Params&, void* field, int col, int right, void* buf, int dir, cudaStream_t);
     cudaError_t (*occupancy)(int tile_shape, int* blocks_per_sm);
 };
 
@@ -43,7 +45,7 @@ constexpr int kSelectStageCap = 8192;
 // Rows and columns per block tile of the shared-memory-staged shapes
 // (rows 0: not staged).
 inline int staged_rows(int tile_shape) {
-    return tile_shape == 4 || tile_shape == 6 ? 8 : (tile_shape == 5 ? 4 : 0);
+    return tile_shape == 4 || tile_shape == 6 ? 8 : (tile_shape == 5 ? 6 : 0);
 }
 inline int staged_cols(int tile_shape) { return tile_shape == 6 ? 64 : 128; }
 

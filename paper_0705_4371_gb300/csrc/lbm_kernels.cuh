@@ -76,14 +76,16 @@ __device__ __forceinline__ void equilibrium_energy(const Params& P, T rho, T jx,
 
 template <typename L, typename T>
 __device__ __forceinline__ void moments(const T* g, T rho0, T& drho, T& rho, T& jx, T& jy) {
-    drho = T(0); jx = T(0); jy = T(0);
-#pragma unroll
-    for (int i = 0; i < L::Q; i++) {
-        drho += g[i];
-        if (L::cx(i) == 1) jx += g[i];
-        if (L::cx(i) == -1) jx -= g[i];
-        if (L::cy(i) == 1) jy += g[i];
-        if (L::cy(i) == -1) jy -= g[i];
+    if constexpr (L::Q == 9) {
+        // pairwise sums (D2Q9 numbering: 1..4 E N W S, 5..8 NE NW SW SE)
+        drho = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7])) + g[8];
+        jx = ((g[1] - g[3]) + (g[5] - g[6])) + (g[8] - g[7]);
+        jy = ((g[2] - g[4]) + (g[5] - g[8])) + (g[6] - g[7]);
+    } else {
+        // D1Q3: 0 rest, 1 left, 2 right
+        drho = (g[0] + g[1]) + g[2];
+        jx = g[2] - g[1];
+        jy = T(0);
     }
     rho = rho0 + drho;
 }
@@ -343,8 +345,9 @@ __device__ __forceinline__ bool update_site(const Params& P, T* g, int x, int y,
 #pragma unroll
     for (int i = 0; i < L::Q; i++) d[i] = g[i] - gs[i];
     if constexpr (PROJ) conserve_neq<L, EQ>(d);
+    // (no short-circuit: the site's update stays one branch-free block)
     const bool pending =
-        P.k > 0 && !ds_cleared<L, T, EQ>(d, gs, rho, ux, uy, Par<T>::rho0(P), Par<T>::delta(P));
+        (P.k > 0) & !ds_cleared<L, T, EQ>(d, gs, rho, ux, uy, Par<T>::rho0(P), Par<T>::delta(P));
     T nb2 = T(-2) * Par<T>::beta(P);
     if constexpr (EQ == EQ_ENTROPIC) {
         if (P.elbm) {
@@ -400,6 +403,7 @@ template <> struct MlpSlot<EQ_ENERGY_MLP> {
 template <typename L, typename S, int EQ>
 __device__ __noinline__ typename Store<S>::T resolve_ds(const Params& P, int x, int y) {
     using T = typename Store<S>::T;
+    if (P.slab && (x < P.own_x0 || x >= P.own_x1)) return T(-1);   // a ghost column
     T g[L::Q], gs[L::Q], rho, ux, uy;
     gather_site<L, S>(P, x, y, g);
     site_equilibrium<L, T, EQ>(P, g, gs, rho, ux, uy);
@@ -444,7 +448,7 @@ __device__ __forceinline__ void warp_push(const Params& P, bool cand, T ds, unsi
 // flushes its buffer to the global list instead (which holds one slot per
 // site and cannot overflow).
 // ---------------------------------------------------------------------------
-constexpr int kBlockCand = 512;
+constexpr int kBlockCand = 320;   // room for a round of 256 candidates above a cut
 
 struct BlockCand {
     unsigned long long key[kBlockCand];
@@ -479,7 +483,7 @@ __device__ __forceinline__ void block_push(const Params& P, BlockCand& bc, bool 
 
 // Keep the k best of the buffer (all threads call; blockDim >= 128).
 static __device__ __noinline__ void block_cut(BlockCand& bc, TopkScratch& sc, int k) {
-    constexpr int kPer = kBlockCand / 128;
+    constexpr int kPer = (kBlockCand + 127) / 128;
     const int tid = threadIdx.x, nt = blockDim.x;
     __syncthreads();
     const int n = (int)min(bc.n, (unsigned)kBlockCand);
@@ -548,7 +552,9 @@ __device__ __forceinline__ void block_finish(const Params& P, BlockCand& bc, Top
 //   mode 0: select among the candidates (or replay a given list), overwrite
 //           the LBGK output of the selected sites with f* (Sec. 3.2; (ESLB)),
 //           log the count and advance the step counter;
-//   mode 1: select only (test hook).
+//   mode 1: select only (the select-only test hook; and a slab's own k best,
+//           with their keys, when the global selection is made across
+//           slabs).
 // Candidates are staged in shared memory when they fit; larger sets are
 // ranked in place in global memory.
 // ---------------------------------------------------------------------------
@@ -577,7 +583,10 @@ __device__ __noinline__ void select_and_fix(const Params& P, SelectShared& ss,
     } else {
         const int n = (int)__ldcg(P.cand_count);
         if (n <= P.k) {
-            for (int j = tid; j < n; j += nt) P.sel_idx[j] = (int)__ldcg(P.cand_idx + j);
+            for (int j = tid; j < n; j += nt) {
+                P.sel_idx[j] = (int)__ldcg(P.cand_idx + j);
+                if (P.sel_key) P.sel_key[j] = __ldcg(P.cand_key + j);
+            }
             if (tid == 0) ss.nsel = n;
         } else {
             const bool staged = n <= stage_cap;
@@ -595,9 +604,13 @@ __device__ __noinline__ void select_and_fix(const Params& P, SelectShared& ss,
             __syncthreads();
             for (int j = tid; j < n; j += nt) {
                 const unsigned id = idat(j);
-                if (th.selected(keyat(j), id)) {
+                const unsigned long long key = keyat(j);
+                if (th.selected(key, id)) {
                     const unsigned s = atomicAdd(&ss.cnt, 1u);
-                    if (s < (unsigned)P.k) P.sel_idx[s] = (int)id;   // exactly k; bounds the write
+                    if (s < (unsigned)P.k) {   // exactly k; bounds the write
+                        P.sel_idx[s] = (int)id;
+                        if (P.sel_key) P.sel_key[s] = key;
+                    }
                 }
             }
             if (tid == 0) ss.nsel = P.k;
@@ -659,8 +672,9 @@ struct FinishShared {
     int is_last;
 };
 
-// Warp-level append of pending sites to the block list (overflow: global).
-__device__ __forceinline__ void warp_pend(const Params& P, unsigned* list, unsigned* nlist, bool pend,
+// Warp-level append of pending sites to the block list of capacity cap
+// (overflow: global).
+__device__ __forceinline__ void warp_pend(const Params& P, unsigned* list, unsigned* nlist, int cap, bool pend,
                                           unsigned site) {
     const unsigned m = __ballot_sync(0xffffffffu, pend);
     if (m == 0) return;
@@ -670,12 +684,12 @@ __device__ __forceinline__ void warp_pend(const Params& P, unsigned* list, unsig
     base = __shfl_sync(0xffffffffu, base, 0);
     if (pend) {
         const unsigned slot = base + __popc(m & ((1u << lane) - 1u));
-        if (slot < (unsigned)kPend) list[slot] = site;
+        if (slot < (unsigned)cap) list[slot] = site;
         else P.pend_idx[atomicAdd(P.pend_count, 1u)] = site;
     }
 }
 __device__ __forceinline__ void warp_pend(const Params& P, FinishShared& fs, bool pend, unsigned site) {
-    warp_pend(P, fs.pend, &fs.npend, pend, site);
+    warp_pend(P, fs.pend, &fs.npend, kPend, pend, site);
 }
 
 // Exact dS of n pending sites, appending the candidates to the block's
@@ -700,11 +714,11 @@ __device__ void resolve_list(const Params& P, int n, SiteAt site_at, BlockCand* 
 }
 
 template <typename L, typename S, int EQ>
-__device__ __forceinline__ void finish_parts(const Params& P, const unsigned* pend, unsigned npend,
+__device__ __forceinline__ void finish_parts(const Params& P, const unsigned* pend, unsigned npend, int pend_cap,
                                              int& is_last, SelectShared& ss, BlockCand& bc,
                                              unsigned long long* stage_key, unsigned* stage_idx,
                                              int stage_cap) {
-    const int np = (int)min(npend, (unsigned)kPend);
+    const int np = (int)min(npend, (unsigned)pend_cap);
     if (np > 0) resolve_list<L, S, EQ>(P, np, [&](int j) { return pend[j]; }, &bc, &ss.sc);
     block_finish(P, bc, ss.sc);
     // the barrier makes the block's writes visible to thread 0, whose
@@ -727,7 +741,7 @@ __device__ __forceinline__ void finish_parts(const Params& P, const unsigned* pe
             if (threadIdx.x == 0) *P.pend_count = 0;
         }
         __threadfence_block();
-        select_and_fix<L, S, EQ>(P, ss, stage_key, stage_idx, stage_cap, 0);
+        select_and_fix<L, S, EQ>(P, ss, stage_key, stage_idx, stage_cap, P.slab ? 1 : 0);
         if (threadIdx.x == 0) {
             *P.ticket = 0;
             if (P.tile_counter) *P.tile_counter = 0;
@@ -738,7 +752,7 @@ __device__ __forceinline__ void finish_parts(const Params& P, const unsigned* pe
 template <typename L, typename S, int EQ>
 __device__ __forceinline__ void finish_block(const Params& P, FinishShared& fs) {
     __syncthreads();
-    finish_parts<L, S, EQ>(P, fs.pend, fs.npend, fs.is_last, fs.ss, fs.bc, fs.key, fs.idx, kStage);
+    finish_parts<L, S, EQ>(P, fs.pend, fs.npend, kPend, fs.is_last, fs.ss, fs.bc, fs.key, fs.idx, kStage);
 }
 
 // Boundary site (or any site of the first step after a state upload): gather
@@ -863,6 +877,47 @@ template <> struct VecIO<plain32, 4> {
 template <> struct VecIO<plain32, 2> {
     __device__ static void load(const void* p, long long i, float* v) { VecIO<float, 2>::load(p, i, v); }
     __device__ static void store(void* p, long long i, const float* v) { VecIO<float, 2>::store(p, i, v); }
+};
+
+// Two adjacent populations (columns c, c + 1 with c even: 8-byte aligned
+// for FP32, 4-byte for FP16, 16-byte for FP64) of a staged plane row or of
+// a population plane, loaded or stored with one access.
+template <typename S> struct PairIO;
+template <> struct PairIO<float> {
+    __device__ static void load(const float* p, float& a, float& b) {
+        const float2 v = *reinterpret_cast<const float2*>(p);
+        a = v.x;
+        b = v.y;
+    }
+    __device__ static void store(float* p, float a, float b) { *reinterpret_cast<float2*>(p) = make_float2(a, b); }
+};
+template <> struct PairIO<plain32> {
+    __device__ static void load(const plain32* p, float& a, float& b) {
+        PairIO<float>::load(reinterpret_cast<const float*>(p), a, b);
+    }
+    __device__ static void store(plain32* p, float a, float b) {
+        PairIO<float>::store(reinterpret_cast<float*>(p), a, b);
+    }
+};
+template <> struct PairIO<__half> {
+    __device__ static void load(const __half* p, float& a, float& b) {
+        const float2 v = __half22float2(*reinterpret_cast<const __half2*>(p));
+        a = v.x;
+        b = v.y;
+    }
+    __device__ static void store(__half* p, float a, float b) {
+        *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a, b);
+    }
+};
+template <> struct PairIO<double> {
+    __device__ static void load(const double* p, double& a, double& b) {
+        const double2 v = *reinterpret_cast<const double2*>(p);
+        a = v.x;
+        b = v.y;
+    }
+    __device__ static void store(double* p, double a, double b) {
+        *reinterpret_cast<double2*>(p) = make_double2(a, b);
+    }
 };
 
 // Interior-path accessors with 32-bit element indices (every population
@@ -1097,9 +1152,12 @@ struct TmaLayout {
     static constexpr int TX_BYTES = 9 * BOX_BYTES;         // bytes one tile's copies deliver
 };
 
+// Shared state of a staged block besides its tiles; NPEND pending sites
+// (room for one tile's sites beyond the drain threshold).
+template <int NPEND>
 struct TmaShared {
     SelectShared ss;
-    unsigned pend[kPend];
+    unsigned pend[NPEND];
     BlockCand bc;
     unsigned npend;
     int is_last;
@@ -1107,9 +1165,15 @@ struct TmaShared {
     int tile[8];   // tile held by each stage (-1: none left)
 };
 
+template <int R, int TX>
+constexpr int tma_pend_cap() {
+    return TX * R + 256;
+}
+
 template <typename S, int R, int STAGES, int EQ, int TX = kTmaTX>
 constexpr size_t tma_smem_bytes() {
-    return 128 + (size_t)STAGES * TmaLayout<S, R, TX>::STAGE_BYTES + 8 * STAGES + sizeof(TmaShared) + 16 +
+    return 128 + (size_t)STAGES * TmaLayout<S, R, TX>::STAGE_BYTES + 8 * STAGES +
+           sizeof(TmaShared<tma_pend_cap<R, TX>()>) + 16 +
            (EQ == EQ_ENERGY_MLP ? sizeof(MlpSlot<EQ>) + 16 : 0);
 }
 
@@ -1191,7 +1255,8 @@ __device__ __forceinline__ void gather_site_smem(const Params& P, const S* box, 
 // the interior path is allocated registers on its own).
 template <typename S, int EQ, int R, int TX>
 __device__ __noinline__ void tma_tile_general(const Params& P, const S* box, int x0, int y0, long long t,
-                                              unsigned* pend_list, unsigned* npend, MlpSlot<EQ>& mslot,
+                                              unsigned* pend_list, unsigned* npend, int pend_cap,
+                                              MlpSlot<EQ>& mslot,
                                               bool& nonfinite, NewtonCount& nc, bool clean) {
     using L = D2Q9;
     using T = typename Store<S>::T;
@@ -1250,7 +1315,7 @@ __device__ __noinline__ void tma_tile_general(const Params& P, const S* box, int
                     Store<S>::store(dst + i * plane + o, 0, fluid ? store_round<L, S>(i, g[i]) : g[i]);
             }
         }
-        warp_pend(P, pend_list, npend, pend, (unsigned)(y * P.nx + x));
+        warp_pend(P, pend_list, npend, pend_cap, pend, (unsigned)(y * P.nx + x));
     }
 }
 
@@ -1261,7 +1326,7 @@ __device__ __noinline__ void tma_tile_general(const Params& P, const S* box, int
 // the bound) are appended to the block's list.
 template <typename S, int EQ, int R, int TX = kTmaTX>
 __device__ __forceinline__ void tma_tile(const Params& P, const S* box, int x0, int y0, long long t,
-                                         unsigned* pend_list, unsigned* npend, MlpSlot<EQ>& mslot,
+                                         unsigned* pend_list, unsigned* npend, int pend_cap, MlpSlot<EQ>& mslot,
                                          bool& nonfinite, NewtonCount& nc) {
     using L = D2Q9;
     using T = typename Store<S>::T;
@@ -1283,36 +1348,52 @@ __device__ __forceinline__ void tma_tile(const Params& P, const S* box, int x0, 
     if (clean && !probe_here) {
         const int row = y * nxp + x0;
         const unsigned site0 = (unsigned)(y * P.nx + x0);
-#pragma unroll 2
-        for (int s = 0; s < TX / 32; s++) {
-            const int c = lane + 32 * s;
-            T g[L::Q];
+        // two adjacent sites per lane, columns c and c + 1 (c = 2 l + 64 s):
+        // planes at rest and every store move both with one access, and the
+        // two updates are independent work for the scheduler
+#pragma unroll 1
+        for (int s = 0; s < TX / 64; s++) {
+            const int c = 2 * lane + 64 * s;
+            T ga[L::Q], gb[L::Q];
 #pragma unroll
-            for (int i = 0; i < L::Q; i++) g[i] = Store<S>::load(sb + i * LY::PLANE + c - L::cx(i), 0);
-            bool pend;
+            for (int i = 0; i < L::Q; i++) {
+                const S* q = sb + i * LY::PLANE + c;
+                if (L::cx(i) == 0) {
+                    PairIO<S>::load(q, ga[i], gb[i]);
+                } else {
+                    ga[i] = Store<S>::load(q - L::cx(i), 0);
+                    gb[i] = Store<S>::load(q + 1 - L::cx(i), 0);
+                }
+            }
+            bool pa, pb;
             if constexpr (EQ == EQ_ENERGY_MLP) {
                 float a0[3];
-                mlp_site_start<T>(P, mslot.s, true, g, a0);
-                pend = update_site<L, T, EQ, Store<S>::kProject, false>(P, g, x0 + c, y, t, nonfinite, nc, a0);
+                mlp_site_start<T>(P, mslot.s, true, ga, a0);
+                pa = update_site<L, T, EQ, Store<S>::kProject, false>(P, ga, x0 + c, y, t, nonfinite, nc, a0);
+                mlp_site_start<T>(P, mslot.s, true, gb, a0);
+                pb = update_site<L, T, EQ, Store<S>::kProject, false>(P, gb, x0 + c + 1, y, t, nonfinite, nc, a0);
             } else {
-                pend = update_site<L, T, EQ, Store<S>::kProject, false>(P, g, x0 + c, y, t, nonfinite, nc);
+                pa = update_site<L, T, EQ, Store<S>::kProject, false>(P, ga, x0 + c, y, t, nonfinite, nc);
+                pb = update_site<L, T, EQ, Store<S>::kProject, false>(P, gb, x0 + c + 1, y, t, nonfinite, nc);
             }
 #pragma unroll
             for (int i = 0; i < L::Q; i++)
-                Store<S>::store(dst + i * plane + row + c, 0, store_round<L, S>(i, g[i]));
-            warp_pend(P, pend_list, npend, pend, site0 + (unsigned)c);
+                PairIO<S>::store(dst + i * plane + row + c, store_round<L, S>(i, ga[i]),
+                                 store_round<L, S>(i, gb[i]));
+            warp_pend(P, pend_list, npend, pend_cap, pa, site0 + (unsigned)c);
+            warp_pend(P, pend_list, npend, pend_cap, pb, site0 + (unsigned)c + 1u);
         }
         return;
     }
-    tma_tile_general<S, EQ, R, TX>(P, box, x0, y0, t, pend_list, npend, mslot, nonfinite, nc, clean);
+    tma_tile_general<S, EQ, R, TX>(P, box, x0, y0, t, pend_list, npend, pend_cap, mslot, nonfinite, nc, clean);
 }
-// Resident blocks per SM the staged kernel is compiled for: two (128
-// registers per thread) in general; three (85 registers per thread) where
-// the tiles take half the shared memory: FP16 storage, or FP32 tiles 64
-// sites wide.
+// Resident blocks per SM the staged kernel is compiled for: two in general
+// (128 registers per thread with 8-row tiles, 170 with 6-row tiles); three
+// (85 registers per thread) where the tiles take half the shared memory:
+// FP16 storage, or FP32 tiles 64 sites wide.
 template <typename S, int R, int TX>
 constexpr int tma_min_blocks() {
-    return (sizeof(S) == 2 && R == 8) || (sizeof(S) == 4 && TX == 64 && R == 8) ? 3 : 16 / R;
+    return (sizeof(S) == 2 && R == 8) || (sizeof(S) == 4 && TX == 64 && R == 8) ? 3 : 2;
 }
 
 template <typename S, int EQ, int R, int STAGES, int TX = kTmaTX>
@@ -1325,8 +1406,10 @@ __global__ void __launch_bounds__(32 * R, tma_min_blocks<S, R, TX>())
     unsigned char* smem = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
     S* stages = reinterpret_cast<S*>(smem);
     unsigned long long* full = reinterpret_cast<unsigned long long*>(smem + STAGES * LY::STAGE_BYTES);
-    TmaShared& sh = *reinterpret_cast<TmaShared*>(smem + STAGES * LY::STAGE_BYTES + 8 * STAGES);
-    constexpr size_t kMlpOff = (STAGES * LY::STAGE_BYTES + 8 * STAGES + sizeof(TmaShared) + 15) / 16 * 16;
+    constexpr int kPendT = tma_pend_cap<R, TX>();
+    using Shared = TmaShared<kPendT>;
+    Shared& sh = *reinterpret_cast<Shared*>(smem + STAGES * LY::STAGE_BYTES + 8 * STAGES);
+    constexpr size_t kMlpOff = (STAGES * LY::STAGE_BYTES + 8 * STAGES + sizeof(Shared) + 15) / 16 * 16;
     MlpSlot<EQ>& mslot = *reinterpret_cast<MlpSlot<EQ>*>(smem + kMlpOff);
     if (threadIdx.x == 0) {
         for (int st = 0; st < STAGES; st++) mbar_init(&full[st], 1);
@@ -1391,8 +1474,8 @@ __global__ void __launch_bounds__(32 * R, tma_min_blocks<S, R, TX>())
         // last block alone would resolve).  npend is read after the barrier
         // above, with no writes to it until the next tile: the branch is
         // uniform.
-        if (sh.npend > (unsigned)(kPend - TX * R)) {
-            resolve_list<L, S, EQ>(P, (int)min(sh.npend, (unsigned)kPend),
+        if (sh.npend > (unsigned)(kPendT - TX * R)) {
+            resolve_list<L, S, EQ>(P, (int)min(sh.npend, (unsigned)kPendT),
                                    [&](int j) { return sh.pend[j]; }, &sh.bc, &sh.ss.sc);
             __syncthreads();
             if (threadIdx.x == 0) sh.npend = 0;
@@ -1409,7 +1492,7 @@ __global__ void __launch_bounds__(32 * R, tma_min_blocks<S, R, TX>())
         }
         const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
         const S* box = stages + (size_t)st * (LY::STAGE_BYTES / sizeof(S));
-        tma_tile<S, EQ, R, TX>(P, box, tx * TX, ty * R, t, sh.pend, &sh.npend, mslot, nonfinite, nc);
+        tma_tile<S, EQ, R, TX>(P, box, tx * TX, ty * R, t, sh.pend, &sh.npend, kPendT, mslot, nonfinite, nc);
     }
     __syncthreads();
     if (sh.abort && threadIdx.x == 0) {
@@ -1427,7 +1510,7 @@ __global__ void __launch_bounds__(32 * R, tma_min_blocks<S, R, TX>())
     const int scap = (int)min((size_t)kStage, (size_t)STAGES * LY::STAGE_BYTES / 12);
     unsigned long long* skey = reinterpret_cast<unsigned long long*>(smem);
     unsigned* sidx = reinterpret_cast<unsigned*>(smem + 8 * scap);
-    finish_parts<L, S, EQ>(P, sh.pend, sh.npend, sh.is_last, sh.ss, sh.bc, skey, sidx, scap);
+    finish_parts<L, S, EQ>(P, sh.pend, sh.npend, kPendT, sh.is_last, sh.ss, sh.bc, skey, sidx, scap);
 }
 
 // ---------------------------------------------------------------------------
@@ -1650,12 +1733,27 @@ __global__ void k_export(const __grid_constant__ Params P, int mode, double* o0,
     }
 }
 
+// Ghost exchange of a slab (runs sharded in x): copies the three
+// populations that cross a face -- moving right (v_x = +1: 1, 5, 8) or left
+// (v_x = -1: 3, 6, 7) -- of column col of the field, between the field and
+// a packed buffer [3][ny] (dir 0: field -> buffer; 1: buffer -> field).
+template <typename S>
+__global__ void k_ghost(const __grid_constant__ Params P, S* field, int col, int right, S* buf, int dir) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= 3 * P.ny) return;
+    const int p = j / P.ny, y = j - p * P.ny;
+    const int plane = right ? (p == 0 ? 1 : (p == 1 ? 5 : 8)) : (p == 0 ? 3 : (p == 1 ? 6 : 7));
+    S* at = field + plane * P.plane + (long long)y * P.nxp + col;
+    if (dir == 0) buf[j] = *at;
+    else *at = buf[j];
+}
+
 // ---------------------------------------------------------------------------
 // Launchers for one storage type.  Tile shapes of the D2Q9 kernel (sites per
 // thread in x, warps per block, minimum resident blocks per SM):
 //   0: 1, 8, 3     1: 1, 8, 4     2: 2, 8, 2     3: 4, 8, 1
 // and of the staged kernel (rows x columns per block tile, tiles in flight):
-//   4: 8 x 128, 2     5: 4 x 128, 3     6: 8 x 64, 2
+//   4: 8 x 128, 2     5: 6 x 128, 3     6: 8 x 64, 2
 // The persistent grid is (resident blocks per SM) x (SM count), from the
 // occupancy calculator, capped by the number of tiles (small grids then
 // spread over as many SMs as they have tiles: their step is latency-bound).
@@ -1703,8 +1801,10 @@ struct LaunchImpl {
         if constexpr (L::Q == 9 && EQ >= EQ_ENERGY) {
             // the energy forms are built for two register-fed shapes (0: two
             // resident blocks, 128 registers per thread; 1-3: four, 64) and
-            // one staged shape
-            if (shape >= 4) return launch_d2q9_tma<S, EQ, 8, 2>(P, tmap, st);
+            // two staged shapes (5: 6-row tiles, 168 registers; 4: 8-row
+            // tiles, 128); shape 6 is refused for them by the host
+            if (shape == 5) return launch_d2q9_tma<S, EQ, 6, 3>(P, tmap, st);
+            if (shape == 4) return launch_d2q9_tma<S, EQ, 8, 2>(P, tmap, st);
             if (shape == 0) return launch_d2q9<S, EQ, 1, 8, 2>(P, st);
             return launch_d2q9<S, EQ, 1, 8, 4>(P, st);
         } else if constexpr (L::Q == 9) {
@@ -1713,7 +1813,7 @@ struct LaunchImpl {
                 case 2: return launch_d2q9<S, EQ, 2, 8, 2>(P, st);
                 case 3: return launch_d2q9<S, EQ, 4, 8, 1>(P, st);
                 case 4: return launch_d2q9_tma<S, EQ, 8, 2>(P, tmap, st);
-                case 5: return launch_d2q9_tma<S, EQ, 4, 3>(P, tmap, st);
+                case 5: return launch_d2q9_tma<S, EQ, 6, 3>(P, tmap, st);
                 case 6: return launch_d2q9_tma<S, EQ, 8, 2, 64>(P, tmap, st);
                 default: return launch_d2q9<S, EQ, 1, 8, 3>(P, st);
             }
@@ -1729,7 +1829,8 @@ struct LaunchImpl {
     static cudaError_t occupancy(int shape, int* per_sm) {
         *per_sm = 1;
         if constexpr (L::Q == 9 && EQ >= EQ_ENERGY) {
-            if (shape >= 4) return setup_d2q9_tma<S, EQ, 8, 2>(per_sm);
+            if (shape == 5) return setup_d2q9_tma<S, EQ, 6, 3>(per_sm);
+            if (shape == 4) return setup_d2q9_tma<S, EQ, 8, 2>(per_sm);
             if (shape == 0) return occupancy_d2q9<S, EQ, 1, 8, 2>(per_sm);
             return occupancy_d2q9<S, EQ, 1, 8, 4>(per_sm);
         } else if constexpr (L::Q == 9) {
@@ -1738,7 +1839,7 @@ struct LaunchImpl {
                 case 2: return occupancy_d2q9<S, EQ, 2, 8, 2>(per_sm);
                 case 3: return occupancy_d2q9<S, EQ, 4, 8, 1>(per_sm);
                 case 4: return setup_d2q9_tma<S, EQ, 8, 2>(per_sm);
-                case 5: return setup_d2q9_tma<S, EQ, 4, 3>(per_sm);
+                case 5: return setup_d2q9_tma<S, EQ, 6, 3>(per_sm);
                 case 6: return setup_d2q9_tma<S, EQ, 8, 2, 64>(per_sm);
                 default: return occupancy_d2q9<S, EQ, 1, 8, 3>(per_sm);
             }
@@ -1767,6 +1868,13 @@ struct LaunchImpl {
         k_export<L, S, EQ><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(P, mode, o0, o1, o2, o3);
         return cudaGetLastError();
     }
+    static cudaError_t ghost(const Params& P, void* field, int col, int right, void* buf, int dir,
+                             cudaStream_t st) {
+        const int n = 3 * P.ny;
+        k_ghost<S><<<(n + 255) / 256, 256, 0, st>>>(P, static_cast<S*>(field), col, right, static_cast<S*>(buf),
+                                                   dir);
+        return cudaGetLastError();
+    }
     static cudaError_t set_smem(int stage_cap) {
         const size_t smem = (size_t)stage_cap * (sizeof(unsigned long long) + sizeof(unsigned));
         return cudaFuncSetAttribute(k_select<L, S, EQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1780,6 +1888,7 @@ struct LaunchImpl {
         l.import_state = &import_state;
         l.export_state = &export_state;
         l.set_smem = &set_smem;
+        l.ghost = &ghost;
         l.occupancy = &occupancy;
         return l;
     }

@@ -128,11 +128,11 @@ def oscillation(rho):
 # Small cases for profiling (python -m paper_0705_4371_gb300.experiments ...)
 # --------------------------------------------------------------------------
 
-def energy_case(eq, steps=3, nx=512, ny=256):
+def energy_case(eq, steps=3, nx=512, ny=256, shape=None):
     """The energy-constrained cylinder (L = ny/16, Re 5000, k 64) with the
     smooth energy pattern, FP32 storage, `steps` directly launched steps; eq 3
-    first trains a network on 2e6 samples.  Prints the kernel time and Newton
-    iterations."""
+    first trains a network on 2e6 samples; shape: tile shape (None: the
+    default).  Prints the kernel time and Newton iterations."""
     w = inputs.cylinder(nx, ny, ny // 16, 5000.0, k=64, eq=inputs.EQ_ENERGY)
     rho, ux, uy = inputs.cylinder_fields(w, noise=1e-2)
     with lbm.Lattice.from_workload(w, precision=lbm.LB_F64) as iso:
@@ -143,14 +143,17 @@ def energy_case(eq, steps=3, nx=512, ny=256):
             from . import learned
             p, _ = learned.train_energy_mlp(n=2_000_000, epochs=10, batch=4096, lr0=2e-3, lr1=2e-5)
             g.set_mlp(p)
+        if shape is not None:
+            g.set_tile_shape(shape)
         g.init_equilibrium(rho, ux, uy, e2)
         g.set_timing(True)
         g.step(steps)
         g.sync()
         kt = g.kernel_times()
         s = g.newton_stats()
-        print("energy case eq %d: %.4f ms per launch, FP32 / high-precision Newton iterations per site %.3f / %.3f"
-              % (eq, kt["collide_ms"] / kt["collide_launches"], s[0] / s[2], s[1] / s[2]))
+        print("energy case eq %d shape %d: %.4f ms per launch, FP32 / high-precision Newton iterations per site"
+              " %.3f / %.3f" % (eq, g.info()["tile_shape"], kt["collide_ms"] / kt["collide_launches"], s[0] / s[2],
+                               s[1] / s[2]))
 
 
 def elbm_case(steps=44, nx=1024, ny=512, precision=lbm.LB_F32):
@@ -201,6 +204,36 @@ def paper_cylinder(re, k=10, delta=1e-3, wall=inputs.WALL_BOUNCE_BACK, steps=Non
     return r
 
 
+# One-at-a-time changes of the 600 x 500 cylinder workload (L = 20, face at
+# 5L, polynomial f*, zero-gradient outflow, bounce-back cylinder, k = 16,
+# delta = 1e-3): the outlet rule (the paper's equilibrium outlet instead of
+# the zero-gradient copy), the cylinder wall (diffuse kinetic wall), the
+# quasiequilibrium (the entropic f* the paper's cylinder runs use), the
+# cylinder position (face at 10L, the paper's centre at 10.5L), and the
+# regulariser (k = L/2 = 10 as in the paper; or k = 100 with delta = 1e-4).
+C2_VARIANTS = {
+    "c2": {},
+    "equilibrium_outlet": {"outlet": inputs.BC_OUTLET},
+    "diffuse_wall": {"wall": inputs.WALL_DIFFUSE},
+    "entropic_f": {"eq": inputs.EQ_ENTROPIC},
+    "face_at_10L": {"face_x": 200},
+    "k10": {"k": 10},
+    "k100_delta1e-4": {"k": 100, "delta": 1e-4},
+}
+
+
+def c2_variant(re, name, steps=200000, precision=lbm.LB_F32):
+    """One C2_VARIANTS case at Reynolds number re, run for `steps` steps or
+    until non-finite."""
+    kw = dict(outlet=inputs.BC_OUTLET_COPY)
+    kw.update(C2_VARIANTS[name])
+    w = inputs.cylinder(600, 500, 20, re, name="c2_%s_Re%g" % (name, re), **kw)
+    r = cylinder_run(w, steps, precision=precision, chunk=10000)
+    r.pop("probe_tail", None)
+    r["variant"] = name
+    return r
+
+
 def main(argv=None):
     import argparse
     ap = argparse.ArgumentParser(description="GPU cases: profiling cases of the learned and batched forms "
@@ -211,6 +244,7 @@ def main(argv=None):
     e.add_argument("--steps", type=int, default=3)
     e.add_argument("--nx", type=int, default=512)
     e.add_argument("--ny", type=int, default=256)
+    e.add_argument("--shape", type=int, default=None)
     el = sub.add_parser("elbm")
     el.add_argument("--steps", type=int, default=44)
     el.add_argument("--nx", type=int, default=1024)
@@ -224,6 +258,9 @@ def main(argv=None):
     c.add_argument("--collision", choices=["lbgk", "elbm"], default="lbgk")
     sh = sub.add_parser("shock")
     sh.add_argument("--steps", type=int, default=400)
+    ab = sub.add_parser("c2ablation")
+    ab.add_argument("--re", type=float, nargs="+", default=[5000.0, 20000.0])
+    ab.add_argument("--steps", type=int, default=200000)
     b = sub.add_parser("batch")
     b.add_argument("--runs", type=int, default=24)
     b.add_argument("--steps", type=int, default=44)
@@ -231,7 +268,7 @@ def main(argv=None):
     a = ap.parse_args(argv)
     lbm.load()
     if a.case == "energy":
-        energy_case(a.eq, a.steps, a.nx, a.ny)
+        energy_case(a.eq, a.steps, a.nx, a.ny, a.shape)
     elif a.case == "elbm":
         elbm_case(a.steps, a.nx, a.ny)
     elif a.case == "shock":
@@ -240,6 +277,11 @@ def main(argv=None):
         for name in sorted(SHOCK_PANELS):
             r, _, counts = shock_panel(name, a.steps)
             print("panel %s: excess TV of rho %.4f, Ehrenfests' sites %d" % (name, oscillation(r), int(counts.sum())))
+    elif a.case == "c2ablation":
+        import json
+        for re in a.re:
+            for name in C2_VARIANTS:
+                print(json.dumps(c2_variant(re, name, a.steps)), flush=True)
     elif a.case == "cylinder":
         import json
         wall = inputs.WALL_DIFFUSE if a.wall == "diffuse" else inputs.WALL_BOUNCE_BACK

@@ -103,6 +103,11 @@ def load(path=None):
         "lb_mlp_grad": ([vp, vp, vp, ip, vp, vp, vp], ip),
         "lb_mlp_adam": ([vp, vp, vp, vp, C.c_longlong, dp, vp], ip),
         "lb_mlp_train": ([vp, vp, vp, C.c_longlong, ip, ip, dp, dp, vp, vp], ip),
+        "lb_set_slab": ([H, ip, ip, ip, ip], ip),
+        "lb_slab_collide": ([H], ip),
+        "lb_slab_candidates": ([H, vp, vp, ip, C.POINTER(ip)], ip),
+        "lb_slab_apply": ([H, vp, ip], ip),
+        "lb_slab_ghost": ([H, ip, vp, ip], ip),
         "lb_last_error": ([], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -392,6 +397,35 @@ class Lattice:
                                       int(reset)))
         return {"collide_ms": cm.value, "collide_launches": cn.value,
                 "select_ms": sm.value, "select_launches": sn.value}
+
+    # slabs of a run sharded in x (lb_set_slab ... lb_slab_ghost)
+    def set_slab(self, ghost_left, ghost_right, global_x0, global_nx):
+        """Make the run a slab of a run sharded in x (lb_set_slab)."""
+        _check(self.L.lb_set_slab(self.h, int(ghost_left), int(ghost_right), int(global_x0), int(global_nx)))
+
+    def slab_collide(self):
+        """Queue the slab's stream + collide launch (lb_slab_collide)."""
+        _check(self.L.lb_slab_collide(self.h))
+
+    def slab_candidates(self, cap):
+        """The slab's best candidates of the collided step: (uint64 keys, int64 global site
+        indices) (lb_slab_candidates)."""
+        keys = np.zeros(max(1, cap), np.uint64)
+        idx = np.zeros(max(1, cap), np.int64)
+        cnt = C.c_int(0)
+        _check(self.L.lb_slab_candidates(self.h, _ptr(keys), _ptr(idx), int(cap), C.byref(cnt)))
+        m = min(cnt.value, cap)
+        return keys[:m].copy(), idx[:m].copy()
+
+    def slab_apply(self, global_idx):
+        """Apply the step's global selection and complete the step (lb_slab_apply)."""
+        g = np.ascontiguousarray(global_idx, np.int64)
+        _check(self.L.lb_slab_apply(self.h, _ptr(g), g.size))
+
+    def slab_ghost(self, side, buf_ptr, direction):
+        """Pack (direction 0) or unpack (1) a side's crossing populations to / from a device
+        buffer given as an integer pointer (lb_slab_ghost)."""
+        _check(self.L.lb_slab_ghost(self.h, int(side), C.c_void_p(buf_ptr), int(direction)))
 
     def set_tile_shape(self, shape):
         """Tile shape of the D2Q9 stream-collide kernel (0-6; lb_set_tile_shape); results do not

@@ -65,3 +65,41 @@ def test_paper_cylinder_setup_runs(lbm):
         r = experiments.paper_cylinder(1000.0, k=4, delta=1e-4, steps=3000, L=8, collision=coll)
         assert r["diverged_at"] is None and r["steps"] == 3000
         assert r["collision"] == coll and r["strouhal"] is not None
+
+
+def test_plain_lbgk_diverges_where_ehrenfests_steps_keep_the_run(lbm):
+    # Sec. 4.2, end of the cylinder results: at L = 20 plain LBGK diverges
+    # near Re = 1000, while a handful of Ehrenfests' steps per time step keep
+    # the same run finite.  The paper's layout (30L x 25L, cylinder centre at
+    # 10.5L, entropic f*, zero-gradient outflow), FP32 storage, 30000 steps.
+    from paper_0705_4371_gb300 import experiments
+    plain = experiments.paper_cylinder(1000.0, k=0, steps=30000)
+    reg = experiments.paper_cylinder(1000.0, k=10, delta=1e-3, steps=30000)
+    print("Re 1000, L 20: plain LBGK non-finite by step %s; with Ehrenfests' steps %s (%.2f sites per step)"
+          % (plain["diverged_at"], reg["diverged_at"], reg["selected_per_step"]))
+    assert plain["diverged_at"] is not None
+    assert reg["diverged_at"] is None and reg["selected_per_step"] > 0
+
+
+def _golden_c2_strouhal():
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "c2_re1000_strouhal.txt")
+    with open(path) as fh:
+        return float([ln for ln in fh if not ln.startswith("#")][0])
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_c2_strouhal_matches_the_oracle_run(lbm, prec):
+    # the 600 x 500 channel of the cylinder workload (L = 20 at 5L, polynomial
+    # f*, zero-gradient outflow, Re = 1000, k = 16, delta = 1e-3) for its full
+    # 2e5 steps: the Strouhal number of the GPU's free run against the FP64
+    # oracle's (tests/golden/c2_re1000_strouhal.txt, written by the script
+    # beside it from the oracle alone), within 1 %
+    from paper_0705_4371_gb300 import experiments
+    st_o = _golden_c2_strouhal()
+    w = inputs.workload_c2(1000.0)
+    r = experiments.cylinder_run(w, 200000, precision=lbm.PRECISIONS[prec], chunk=20000)
+    assert r["diverged_at"] is None
+    print("c2 Re 1000 Strouhal %s: GPU %.5f oracle %.5f (%.3f %%)"
+          % (prec, r["strouhal"], st_o, 100 * abs(r["strouhal"] - st_o) / st_o))
+    assert abs(r["strouhal"] - st_o) <= 0.01 * st_o

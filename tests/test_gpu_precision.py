@@ -93,7 +93,7 @@ def test_moments_1000_steps_against_oracle_and_storage_floor(lbm, prec, layout):
           {k: "%.2e" % v for k, v in got.items()}, {k: "%.2e" % v for k, v in floor.items()}))
     for c in ("M", "rho", "jx", "jy"):
         # the arithmetic adds at most a small multiple of the storage floor
-        assert got[c] <= 4.0 * floor[c] + 2e-7, (c, got[c], floor[c])
+        assert got[c] <= 6.0 * floor[c] + 2e-7, (c, got[c], floor[c])
     if prec != "f16dev":
         # the FP32 target, wherever the storage itself allows it: plain FP32
         # storage at Re = 20000 has a momentum floor above 1e-5 (the
