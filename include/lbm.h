@@ -341,9 +341,9 @@ int lb_kernel_times(lb_handle* h, double* collide_ms, long long* collide_launche
  * deviation);  6 = 8 x 64, STAGES 2 (three blocks per SM).  The
  * energy-constrained forms are built for shapes 0 (1, 8, 2: 128 registers
  * per thread), 1 (2 and 3 run 1), 4 and 5, and refuse 6 (LB_ERR_ARG); their
- * defaults: 1 for FP64 storage, 4 for the Newton start and 0 for the
- * network's warm start in FP32 / FP16 storage.  Results do not depend on
- * the shape; only the speed does. */
+ * defaults: 1 for FP64 storage, 4 for FP32 / FP16 storage (Newton start and
+ * network warm start alike).  Results do not depend on the shape; only the
+ * speed does. */
 int lb_set_tile_shape(lb_handle* h, int shape);
 
 /* ------------------------------------------------------------------------

@@ -49,15 +49,15 @@ constexpr int kDefaultLog = 65536;
 // 5); FP16 and FP64 storage 8-row tiles with 1 more (shape 4; FP16 with
 // three blocks per SM).  The energy forms are bound by the Newton solve, not
 // by memory: FP64 storage's FP64 finish wants the most resident warps
-// (register-fed shape 1); the float-float finish of FP32 / FP16 storage runs
-// best in the staged shape 4, and the network's warm start in the
-// register-fed shape with 128 registers (shape 0), where its fragments spill
-// least.
+// (register-fed shape 1); the float-float finish of FP32 / FP16 storage and
+// the network's warm start run best in the staged shape 4 (measured at
+// 2048 x 1024: Newton start 0.22 ms per step against 0.44 on shape 0 and 0.24
+// on shape 5; warm start 0.35 against 0.54 and 0.35).
 int default_tile_shape(int lattice, int eq, int precision) {
     if (lattice != LB_D2Q9) return 0;
     if (eq < LB_EQ_ENTROPIC_ENERGY) return (precision == LB_F32 || precision == LB_F32_DEV) ? 5 : 4;
     if (precision == LB_F64) return 1;
-    return eq == LB_EQ_ENTROPIC_ENERGY_MLP ? 0 : 4;
+    return 4;
 }
 
 size_t storage_bytes(int prec) { return prec == LB_F64 ? 8 : (prec == LB_F16_DEV ? 2 : 4); }

@@ -127,12 +127,12 @@ def test_energy_run_replayed_selection(lbm, prec):
 @pytest.mark.parametrize("prec", ["f32", "f16dev", "f64"])
 def test_energy_tile_shapes_give_identical_results(lbm, prec):
     # the energy forms' register-fed shapes (0: 128 registers, 1: 64) and the
-    # staged shape 4 run the same per-site arithmetic; a noisy start puts
+    # staged shapes 4 and 5 run the same per-site arithmetic; a noisy start puts
     # many sites near delta, so the pending lists fill and drain in the loop
     w = energy_cylinder(nx=328, ny=150, L=12, delta=1e-7, k=64)
     rho, ux, uy, e2 = energy_fields(w, 21, noise=2e-2)
     states = {}
-    for shape in (0, 1, 4):
+    for shape in (0, 1, 4, 5):
         g = lbm.Lattice.from_workload(w, precision=lbm.PRECISIONS[prec])
         g.set_tile_shape(shape)
         g.init_equilibrium(rho, ux, uy, e2)
