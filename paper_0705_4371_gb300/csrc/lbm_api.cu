@@ -144,6 +144,8 @@ struct lb_handle {
     // tensor maps of the two population buffers (shared-memory-staged shapes)
     CUtensorMap tmap[2];
     unsigned* tile_counter;
+    // claim order of the staged shapes' tiles: boundary tiles first
+    int* tile_order;
     // slab of a run sharded in x: ghost columns on each side, global x of the
     // first owned column, global nx; the keys of the slab's best candidates;
     // the step's selection among the slab's sites (one replayed step)
@@ -210,6 +212,7 @@ Params make_params(const lb_handle* h, int src, bool prestream) {
     P.pend_count = h->pend_count;
     P.grid_blocks = h->grid_blocks;
     P.tile_counter = h->tile_counter;
+    P.tile_order = h->tile_order;
     P.elbm = h->elbm ? 1 : 0;
     P.wall = h->bc.obstacle_wall;
     P.slab = h->slab;
@@ -327,13 +330,42 @@ int encode_tensor_map(const lb_handle* h, int b, int rows, int cols, CUtensorMap
     return LB_OK;
 }
 
+// Claim order of the staged tiles (rows x cols sites): the tiles that take
+// the rule-by-rule path (the grid's edge rows and columns, the obstacle and
+// its neighbours; the same test as the kernel's) first, row-major, then the
+// interior tiles, row-major.  The slow tiles then run while every block is
+// busy, and the last tiles handed out are interior tiles of equal cost.
+std::vector<int> staged_tile_order(const lb_handle* h, int rows, int cols) {
+    const int tiles_x = (h->nx + cols - 1) / cols, tiles_y = (h->ny + rows - 1) / rows;
+    const lb_boundaries& b = h->bc;
+    std::vector<int> order;
+    order.reserve((size_t)tiles_x * tiles_y);
+    for (int pass = 0; pass < 2; pass++)
+        for (int ty = 0; ty < tiles_y; ty++)
+            for (int tx = 0; tx < tiles_x; tx++) {
+                const int x0 = tx * cols, y0 = ty * rows;
+                const bool clean = x0 >= 1 && x0 + cols <= h->nx - 1 && y0 >= 1 && y0 + rows <= h->ny - 1 &&
+                                   (b.obstacle_w == 0 || x0 + cols + 1 <= b.obstacle_x0 ||
+                                    x0 - 1 >= b.obstacle_x0 + b.obstacle_w || y0 + rows + 1 <= b.obstacle_y0 ||
+                                    y0 - 1 >= b.obstacle_y0 + b.obstacle_h);
+                if (clean == (pass == 1)) order.push_back(ty * tiles_x + tx);
+            }
+    return order;
+}
+
 int make_tensor_maps(lb_handle* h) {
     const int rows = staged_rows(h->tile_shape);
     if (h->lattice != LB_D2Q9 || rows == 0) return LB_OK;
+    const int cols = staged_cols(h->tile_shape);
     for (int b = 0; b < 2; b++) {
-        const int rc = encode_tensor_map(h, b, rows, staged_cols(h->tile_shape), &h->tmap[b]);
+        const int rc = encode_tensor_map(h, b, rows, cols, &h->tmap[b]);
         if (rc != LB_OK) return rc;
     }
+    const std::vector<int> order = staged_tile_order(h, rows, cols);
+    if (h->tile_order) cudaFree(h->tile_order);
+    h->tile_order = nullptr;
+    CK(cudaMalloc(&h->tile_order, order.size() * sizeof(int)));
+    CK(cudaMemcpy(h->tile_order, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice));
     return LB_OK;
 }
 
@@ -413,8 +445,8 @@ void lb_destroy(lb_handle* h) {
     void* ptrs[] = {h->buf[0], h->buf[1], h->cand_key, h->cand_idx, h->cand_count, h->sel_idx,
                     h->sel_count, h->count_ring, h->probe_ring, h->d_step, h->d_err, h->replay_cnt,
                     h->replay_off, h->replay_idx, h->mlp, h->newton_stats, h->ticket,
-                    h->pend_idx, h->pend_count, h->tile_counter, h->stage, h->sel_key, h->slab_sel,
-                    h->slab_cnt, h->slab_off};
+                    h->pend_idx, h->pend_count, h->tile_counter, h->tile_order, h->stage, h->sel_key,
+                    h->slab_sel, h->slab_cnt, h->slab_off};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->h_err) cudaFreeHost(h->h_err);

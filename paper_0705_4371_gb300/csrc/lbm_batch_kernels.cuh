@@ -139,12 +139,13 @@ __global__ void __launch_bounds__(32 * R, 16 / R) k_collide_batch(const __grid_c
         bool nonfinite = false;
         NewtonCount nc = {0, 0, 0, 0};
         const S* box = stages + (size_t)st * (LY::STAGE_BYTES / sizeof(S));
-        tma_tile<S, EQ, R>(P, box, tx * TX, ty * R, t, sh.pend, &sh.npend, kPend, mslot, nonfinite, nc);
+        PendSink sink{sh.pend, &sh.npend, kPend};
+        tma_tile<S, EQ, R>(P, box, tx * TX, ty * R, t, sink, mslot, nonfinite, nc, P);
         const int nf = __syncthreads_or(nonfinite);
         // the tile's pending sites (npend is read between barriers: uniform)
         if (sh.npend > 0) {
             resolve_list<L, S, EQ>(P, (int)min(sh.npend, (unsigned)kPend), [&](int j) { return sh.pend[j]; },
-                                   nullptr, nullptr);
+                                   static_cast<BlockCand*>(nullptr), nullptr);
             __syncthreads();
             if (threadIdx.x == 0) sh.npend = 0;
         }

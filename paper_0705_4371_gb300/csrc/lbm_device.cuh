@@ -113,6 +113,7 @@ struct Params {
     unsigned* pend_count;
     int grid_blocks;          // persistent grid size (resident blocks x SMs)
     unsigned* tile_counter;   // next tile to hand out (staged shapes)
+    const int* tile_order;    // staged shapes: tile of each claim (null: row-major)
     int elbm;                 // ELBM collision (elbmLB) instead of LBGK (entropic f* only)
     int wall;                 // rule on the obstacle's faces: WALL_BOUNCE_BACK / WALL_DIFFUSE
     // slab of a run sharded in x: only columns [own_x0, own_x1) are the

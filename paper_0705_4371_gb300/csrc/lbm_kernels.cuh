@@ -328,14 +328,55 @@ __device__ __noinline__ T elbm_factor(PopArr<L::Q, T> g, PopArr<L::Q, T> gs, T r
     return -a * beta;
 }
 
+// Exact dS of a site from its pre-collision deviations g and its
+// quasiequilibrium gs (rho0, dl: the run's rho0 and delta in T).  The
+// precision form (recheck) decides the sites whose FP32 dS lies within band
+// of delta (a bound on the FP32 evaluation error of dS, set by the host) in
+// FP64; the value kept for ranking then stays on the same side of delta.
+// Returns dS in T (NaN for a non-finite state).  Out of line: the sites the
+// bound does not clear are few, and the update path keeps its registers.
+template <typename L, typename T, int EQ>
+__device__ __noinline__ T resolved_ds(PopArr<L::Q, T> g, PopArr<L::Q, T> gs, T rho0, T dl, double delta,
+                                      double rho0d, double band, int recheck) {
+    T ds = delta_s_exact<L, T>(g.v, gs.v, rho0);
+    if (recheck && isfinite(ds) && fabs((double)ds - delta) <= band) {
+        const double d64 = delta_s_fp64<L, T, EQ>(g, rho0d);
+        if (d64 > delta) ds = (T)d64 > dl ? (T)d64 : nextafter(dl, T(INFINITY));
+        else ds = T(-1);
+    }
+    return ds;
+}
+
+// The same from the site's pre-collision deviations g and quasiequilibrium
+// gs already at hand.
+template <typename L, typename T, int EQ>
+__device__ __forceinline__ T site_ds(const Params& P, const T* g, const T* gs) {
+    PopArr<L::Q, T> ga, gsa;
+#pragma unroll
+    for (int i = 0; i < L::Q; i++) {
+        ga.v[i] = g[i];
+        gsa.v[i] = gs[i];
+    }
+    return resolved_ds<L, T, EQ>(ga, gsa, Par<T>::rho0(P), Par<T>::delta(P), P.delta, P.rho0, P.recheck_band,
+                                 P.recheck);
+}
+
+// A ghost column of a slab (a copy of a neighbour's sites: never a candidate).
+__device__ __forceinline__ bool ghost_column(const Params& P, int x) {
+    return P.slab && (x < P.own_x0 || x >= P.own_x1);
+}
+
 // PROBE = false: the caller guarantees the site is not the probe site.
 // PROJ: remove the rounding defects of the conserved moments of f - f*
 // (conserve_neq; FP32 storage).  g leaves as the deviations to store, before
-// the storage's rounding (store_round).
-template <typename L, typename T, int EQ, bool PROJ, bool PROBE = true>
+// the storage's rounding (store_round).  RESOLVE: a site the bound does not
+// clear has its dS evaluated here, from the pre-collision g and f* at hand
+// (site_ds), and stored to *ds_out (-1 for every other site, and for a
+// slab's ghost columns).
+template <typename L, typename T, int EQ, bool PROJ, bool PROBE = true, bool RESOLVE = false>
 __device__ __forceinline__ bool update_site(const Params& P, T* g, int x, int y, long long t,
                                             bool& nonfinite, NewtonCount& nc,
-                                            const float* a0 = nullptr) {
+                                            const float* a0 = nullptr, T* ds_out = nullptr) {
     T gs[L::Q], rho, ux, uy;
     site_equilibrium<L, T, EQ>(P, g, gs, rho, ux, uy, nc, a0);
     nonfinite |= !isfinite(rho + ux + uy);
@@ -348,6 +389,11 @@ __device__ __forceinline__ bool update_site(const Params& P, T* g, int x, int y,
     // (no short-circuit: the site's update stays one branch-free block)
     const bool pending =
         (P.k > 0) & !ds_cleared<L, T, EQ>(d, gs, rho, ux, uy, Par<T>::rho0(P), Par<T>::delta(P));
+    if constexpr (RESOLVE) {
+        T ds = T(-1);
+        if (pending && !ghost_column(P, x)) ds = site_ds<L, T, EQ>(P, g, gs);
+        *ds_out = ds;
+    }
     T nb2 = T(-2) * Par<T>::beta(P);
     if constexpr (EQ == EQ_ENTROPIC) {
         if (P.elbm) {
@@ -394,30 +440,16 @@ template <> struct MlpSlot<EQ_ENERGY_MLP> {
     __device__ void fill(const Params& P) { mlp_fill(s, P.mlp); }
 };
 
-// Exact dS of site (x, y) from the source field (the pre-collision state is
-// re-gathered; the source is not written during a step).  The precision
-// form decides the sites whose FP32 dS lies within recheck_band of delta
-// (a bound on the FP32 evaluation error of dS, set by the host) in FP64;
-// the value kept for ranking then stays on the same side of delta.  Returns
-// dS in T (NaN for a non-finite state).
+// Exact dS of site (x, y) with the pre-collision state re-gathered from the
+// source field (not written during a step); -1 on a slab's ghost column.
 template <typename L, typename S, int EQ>
 __device__ __noinline__ typename Store<S>::T resolve_ds(const Params& P, int x, int y) {
     using T = typename Store<S>::T;
-    if (P.slab && (x < P.own_x0 || x >= P.own_x1)) return T(-1);   // a ghost column
+    if (ghost_column(P, x)) return T(-1);
     T g[L::Q], gs[L::Q], rho, ux, uy;
     gather_site<L, S>(P, x, y, g);
     site_equilibrium<L, T, EQ>(P, g, gs, rho, ux, uy);
-    T ds = delta_s_exact<L, T>(g, gs, Par<T>::rho0(P));
-    if (P.recheck && isfinite(ds) && fabs((double)ds - P.delta) <= P.recheck_band) {
-        PopArr<L::Q, T> ga;
-#pragma unroll
-        for (int i = 0; i < L::Q; i++) ga.v[i] = g[i];
-        const double d64 = delta_s_fp64<L, T, EQ>(ga, P.rho0);
-        const T dl = Par<T>::delta(P);
-        if (d64 > P.delta) ds = (T)d64 > dl ? (T)d64 : nextafter(dl, T(INFINITY));
-        else ds = T(-1);
-    }
-    return ds;
+    return site_ds<L, T, EQ>(P, g, gs);
 }
 
 // Warp-level append of candidates (sites with dS > delta) to the global
@@ -446,22 +478,29 @@ __device__ __forceinline__ void warp_push(const Params& P, bool cand, T ds, unsi
 // to the global list when it ends.  The global select then ranks at most
 // k x blocks keys.  With k too large for a cut to free room, the block
 // flushes its buffer to the global list instead (which holds one slot per
-// site and cannot overflow).
+// site and cannot overflow).  CAP entries: room for the entries kept by a
+// cut plus one round of appends (a round of pending sites resolved by the
+// block, or the sites of one staged tile).
 // ---------------------------------------------------------------------------
 constexpr int kBlockCand = 320;   // room for a round of 256 candidates above a cut
 
-struct BlockCand {
-    unsigned long long key[kBlockCand];
-    unsigned idx[kBlockCand];
-    unsigned n;          // candidates appended (entries beyond kBlockCand went to the global list)
+template <int CAP>
+struct BlockCandT {
+    static constexpr int kCap = CAP;
+    unsigned long long key[CAP];
+    unsigned idx[CAP];
+    unsigned n;          // candidates appended (entries beyond CAP went to the global list)
     unsigned base;
 };
+using BlockCand = BlockCandT<kBlockCand>;
 
-// Warp-level append to the block's buffer (every lane calls).
-template <typename T>
-__device__ __forceinline__ void block_push(const Params& P, BlockCand& bc, bool cand, T ds, unsigned site) {
+// Warp-level append to the block's buffer (every lane calls).  Returns the
+// number of candidates the warp appended (the same on every lane).
+template <typename T, int CAP>
+__device__ __forceinline__ unsigned block_push(const Params& P, BlockCandT<CAP>& bc, bool cand, T ds,
+                                               unsigned site) {
     const unsigned m = __ballot_sync(0xffffffffu, cand);
-    if (m == 0) return;
+    if (m == 0) return 0u;
     const int lane = threadIdx.x & 31;
     unsigned base = 0;
     if (lane == 0) base = atomicAdd(&bc.n, (unsigned)__popc(m));
@@ -469,7 +508,7 @@ __device__ __forceinline__ void block_push(const Params& P, BlockCand& bc, bool 
     if (cand) {
         const unsigned slot = base + __popc(m & ((1u << lane) - 1u));
         const unsigned long long key = ds_key((double)ds);
-        if (slot < (unsigned)kBlockCand) {
+        if (slot < (unsigned)CAP) {
             bc.key[slot] = key;
             bc.idx[slot] = site;
         } else {
@@ -479,14 +518,16 @@ __device__ __forceinline__ void block_push(const Params& P, BlockCand& bc, bool 
             P.cand_idx[g] = site;
         }
     }
+    return (unsigned)__popc(m);
 }
 
 // Keep the k best of the buffer (all threads call; blockDim >= 128).
-static __device__ __noinline__ void block_cut(BlockCand& bc, TopkScratch& sc, int k) {
-    constexpr int kPer = (kBlockCand + 127) / 128;
+template <int CAP>
+__device__ __noinline__ void block_cut(BlockCandT<CAP>& bc, TopkScratch& sc, int k) {
+    constexpr int kPer = (CAP + 127) / 128;
     const int tid = threadIdx.x, nt = blockDim.x;
     __syncthreads();
-    const int n = (int)min(bc.n, (unsigned)kBlockCand);
+    const int n = (int)min(bc.n, (unsigned)CAP);
     if (n <= k) return;   // uniform: n was read after the barrier
     const Thresh th = block_topk(sc, n, k, [&](int e) { return bc.key[e]; }, [&](int e) { return bc.idx[e]; });
     unsigned long long kk[kPer];
@@ -514,9 +555,10 @@ static __device__ __noinline__ void block_cut(BlockCand& bc, TopkScratch& sc, in
 }
 
 // Move the buffer to the global candidate list (all threads call).
-static __device__ __noinline__ void block_flush(const Params& P, BlockCand& bc) {
+template <int CAP>
+__device__ __noinline__ void block_flush(const Params& P, BlockCandT<CAP>& bc) {
     __syncthreads();
-    const int n = (int)min(bc.n, (unsigned)kBlockCand);
+    const int n = (int)min(bc.n, (unsigned)CAP);
     if (n == 0) return;   // uniform
     if (threadIdx.x == 0) bc.base = atomicAdd(P.cand_count, (unsigned)n);
     __syncthreads();
@@ -531,9 +573,10 @@ static __device__ __noinline__ void block_flush(const Params& P, BlockCand& bc) 
 }
 
 // Make room for another blockDim candidates (all threads call).
-__device__ __forceinline__ void block_room(const Params& P, BlockCand& bc, TopkScratch& sc) {
+template <int CAP>
+__device__ __forceinline__ void block_room(const Params& P, BlockCandT<CAP>& bc, TopkScratch& sc) {
     __syncthreads();
-    const int room = kBlockCand - (int)blockDim.x;
+    const int room = CAP - (int)blockDim.x;
     if ((int)bc.n > room) {   // uniform
         if (P.k <= room) block_cut(bc, sc, P.k);
         else block_flush(P, bc);
@@ -541,7 +584,8 @@ __device__ __forceinline__ void block_room(const Params& P, BlockCand& bc, TopkS
 }
 
 // What the block contributes to the global select: its k best (all threads).
-__device__ __forceinline__ void block_finish(const Params& P, BlockCand& bc, TopkScratch& sc) {
+template <int CAP>
+__device__ __forceinline__ void block_finish(const Params& P, BlockCandT<CAP>& bc, TopkScratch& sc) {
     if (P.k > 0) block_cut(bc, sc, P.k);
     block_flush(P, bc);
 }
@@ -625,8 +669,15 @@ __device__ __noinline__ void select_and_fix(const Params& P, SelectShared& ss,
             if (site < 0 || site >= nsites) { atomicOr(P.err, ERR_REPLAY); continue; }
             const int x = site % P.nx, y = site / P.nx;
             if (is_solid(P, x, y)) { atomicOr(P.err, ERR_REPLAY); continue; }
+            const long long o = (long long)y * P.nxp + x;
+            // f* of the site from its post-collision populations: the
+            // collision conserves every moment f* depends on, so this is f*
+            // of the pre-collision state, read at the site itself (nine
+            // independent loads, no boundary rules: the block that runs this
+            // is alone on the device by then, and its code path stays short)
             T g[L::Q], gs[L::Q], rho, ux, uy;
-            gather_site<L, S>(P, x, y, g);
+#pragma unroll
+            for (int i = 0; i < L::Q; i++) g[i] = Store<S>::load(P.dst, i * P.plane + o);
             site_equilibrium<L, T, EQ>(P, g, gs, rho, ux, uy);
             if constexpr (Store<S>::kProject) {
                 // f' = f* = f - (f - f*), with the conserved moments of
@@ -638,7 +689,6 @@ __device__ __noinline__ void select_and_fix(const Params& P, SelectShared& ss,
 #pragma unroll
                 for (int i = 0; i < L::Q; i++) gs[i] = g[i] - d[i];
             }
-            const long long o = (long long)y * P.nxp + x;
 #pragma unroll
             for (int i = 0; i < L::Q; i++)
                 Store<S>::store(P.dst, i * P.plane + o, store_round<L, S>(i, gs[i]));
@@ -673,11 +723,12 @@ struct FinishShared {
 };
 
 // Warp-level append of pending sites to the block list of capacity cap
-// (overflow: global).
-__device__ __forceinline__ void warp_pend(const Params& P, unsigned* list, unsigned* nlist, int cap, bool pend,
-                                          unsigned site) {
+// (overflow: global).  Returns the number the warp appended (the same on
+// every lane).
+__device__ __forceinline__ unsigned warp_pend(const Params& P, unsigned* list, unsigned* nlist, int cap, bool pend,
+                                              unsigned site) {
     const unsigned m = __ballot_sync(0xffffffffu, pend);
-    if (m == 0) return;
+    if (m == 0) return 0u;
     const int lane = threadIdx.x & 31;
     unsigned base = 0;
     if (lane == 0) base = atomicAdd(nlist, (unsigned)__popc(m));
@@ -687,16 +738,17 @@ __device__ __forceinline__ void warp_pend(const Params& P, unsigned* list, unsig
         if (slot < (unsigned)cap) list[slot] = site;
         else P.pend_idx[atomicAdd(P.pend_count, 1u)] = site;
     }
+    return (unsigned)__popc(m);
 }
-__device__ __forceinline__ void warp_pend(const Params& P, FinishShared& fs, bool pend, unsigned site) {
-    warp_pend(P, fs.pend, &fs.npend, kPend, pend, site);
+__device__ __forceinline__ unsigned warp_pend(const Params& P, FinishShared& fs, bool pend, unsigned site) {
+    return warp_pend(P, fs.pend, &fs.npend, kPend, pend, site);
 }
 
 // Exact dS of n pending sites, appending the candidates to the block's
 // buffer bc (its k best reach the global list) or, with bc null, straight
 // to the global list; all threads call with the same n.
-template <typename L, typename S, int EQ, typename SiteAt>
-__device__ void resolve_list(const Params& P, int n, SiteAt site_at, BlockCand* bc, TopkScratch* sc) {
+template <typename L, typename S, int EQ, typename SiteAt, typename BC = BlockCand>
+__device__ void resolve_list(const Params& P, int n, SiteAt site_at, BC* bc, TopkScratch* sc) {
     using T = typename Store<S>::T;
     const T delta = Par<T>::delta(P);
     for (int b = 0; b < n; b += blockDim.x) {
@@ -713,9 +765,9 @@ __device__ void resolve_list(const Params& P, int n, SiteAt site_at, BlockCand* 
     }
 }
 
-template <typename L, typename S, int EQ>
+template <typename L, typename S, int EQ, typename BC>
 __device__ __forceinline__ void finish_parts(const Params& P, const unsigned* pend, unsigned npend, int pend_cap,
-                                             int& is_last, SelectShared& ss, BlockCand& bc,
+                                             int& is_last, SelectShared& ss, BC& bc,
                                              unsigned long long* stage_key, unsigned* stage_idx,
                                              int stage_cap) {
     const int np = (int)min(npend, (unsigned)pend_cap);
@@ -981,6 +1033,7 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_collide_d2q9(const __grid_
     const int t1 = min(t0 + per_block, tiles);
     bool nonfinite = false;
     NewtonCount nc = {0, 0, 0, 0};
+    unsigned wpend = 0u;   // pending sites this warp appended since the last drain
     // one row tile of 32 * VEC sites: row y, tile column xt
     auto do_tile = [&](int y, int xt) {
         const int x0 = xt * TX;
@@ -1034,7 +1087,7 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_collide_d2q9(const __grid_
                 store_vec<S, VEC>(dst, i * plane + row, v);
             }
 #pragma unroll
-            for (int s = 0; s < VEC; s++) warp_pend(P, fs, pend[s], (unsigned)(y * P.nx + xs + s));
+            for (int s = 0; s < VEC; s++) wpend += warp_pend(P, fs, pend[s], (unsigned)(y * P.nx + xs + s));
         } else {
 #pragma unroll 1
             for (int s = 0; s < VEC; s++) {
@@ -1042,7 +1095,7 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_collide_d2q9(const __grid_
                 int r = 0;
                 if (x < P.nx) r = boundary_site<S, EQ>(P, x, y, t);
                 nonfinite |= (r & 1) != 0;
-                warp_pend(P, fs, (r & 2) != 0, (unsigned)(y * P.nx + x));
+                wpend += warp_pend(P, fs, (r & 2) != 0, (unsigned)(y * P.nx + x));
             }
         }
     };
@@ -1056,11 +1109,14 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_collide_d2q9(const __grid_
         }
     } else {
         // The energy forms go in rounds of one tile per warp and resolve the
-        // block's pending sites once its list could not take another round's
-        // (as the staged kernel does): a start far from equilibrium then
-        // cannot overflow many sites to the global list, which the last
-        // block alone resolves.  npend is read between two barriers with no
-        // writes in between, so the branch is uniform.
+        // block's pending sites before its list could overflow in the next
+        // round: a start far from equilibrium then cannot overflow many sites
+        // to the global list, which the last block alone resolves.  The
+        // block drains once some warp appended more than its share (1 /
+        // WARPS) of the room left for a round; one vote over the warps' own
+        // counts decides, so every warp takes the same branch.
+        static_assert(kPend > TX * WARPS, "a round must fit in the pending list");
+        constexpr unsigned kShare = (unsigned)((kPend - TX * WARPS) / WARPS);
         const int rounds = t1 > t0 ? (t1 - t0 + WARPS - 1) / WARPS : 0;
         for (int r = 0; r < rounds; r++) {
             const int w = t0 + r * WARPS + warp;
@@ -1068,13 +1124,13 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_collide_d2q9(const __grid_
                 const int y = w / tiles_x;
                 do_tile(y, w - y * tiles_x);
             }
-            __syncthreads();
-            if (fs.npend > (unsigned)(kPend - TX * WARPS)) {
+            if (__syncthreads_or(wpend > kShare)) {
                 resolve_list<L, S, EQ>(P, (int)min(fs.npend, (unsigned)kPend),
                                        [&](int j) { return fs.pend[j]; }, &fs.bc, &fs.ss.sc);
                 __syncthreads();
                 if (threadIdx.x == 0) fs.npend = 0;
                 __syncthreads();
+                wpend = 0u;
             }
         }
     }
@@ -1152,30 +1208,62 @@ struct TmaLayout {
     static constexpr int TX_BYTES = 9 * BOX_BYTES;         // bytes one tile's copies deliver
 };
 
-// Shared state of a staged block besides its tiles; NPEND pending sites
-// (room for one tile's sites beyond the drain threshold).
-template <int NPEND>
+// Candidate buffer of a staged block: room for one tile's sites above what
+// a cut keeps (the block cuts between tiles).
+template <int R, int TX>
+constexpr int tma_cand_cap() {
+    return TX * R + kBlockCand;
+}
+
+// Shared state of a staged block besides its tiles.  p: the launch's
+// parameters, for the out-of-line paths (a reference to the kernel's
+// __grid_constant__ parameter passed to a function that is not inlined
+// reads it through generic loads of the parameter space; the shared copy
+// answers at shared-memory latency).
+template <int CAP>
 struct TmaShared {
+    Params p;
     SelectShared ss;
-    unsigned pend[NPEND];
-    BlockCand bc;
-    unsigned npend;
+    BlockCandT<CAP> bc;
     int is_last;
     int abort;
     int tile[8];   // tile held by each stage (-1: none left)
 };
 
-template <int R, int TX>
-constexpr int tma_pend_cap() {
-    return TX * R + 256;
-}
-
 template <typename S, int R, int STAGES, int EQ, int TX = kTmaTX>
 constexpr size_t tma_smem_bytes() {
     return 128 + (size_t)STAGES * TmaLayout<S, R, TX>::STAGE_BYTES + 8 * STAGES +
-           sizeof(TmaShared<tma_pend_cap<R, TX>()>) + 16 +
+           sizeof(TmaShared<tma_cand_cap<R, TX>()>) + 16 +
            (EQ == EQ_ENERGY_MLP ? sizeof(MlpSlot<EQ>) + 16 : 0);
 }
+
+// Where a staged tile's updated sites go (put: every lane of the warp calls,
+// with its site's pending flag and, for a sink that resolves, its dS).
+// PendSink: the sites the dS bound does not clear, to a pending list whose
+// exact dS is evaluated later from the source field.  CandSink: the dS of
+// those sites is evaluated in the update itself (update_site, RESOLVE) and
+// the candidates (dS > delta) go to the block's buffer; count is what the
+// warp appended since the block's last cut (the same on every lane).
+struct PendSink {
+    static constexpr bool kResolve = false;
+    unsigned* list;
+    unsigned* n;
+    int cap;
+    template <typename T>
+    __device__ __forceinline__ void put(const Params& P, bool pending, T, unsigned site) {
+        warp_pend(P, list, n, cap, pending, site);
+    }
+};
+template <int CAP>
+struct CandSink {
+    static constexpr bool kResolve = true;
+    BlockCandT<CAP>* bc;
+    unsigned count;
+    template <typename T>
+    __device__ __forceinline__ void put(const Params& P, bool, T ds, unsigned site) {
+        count += block_push<T>(P, *bc, ds > Par<T>::delta(P), ds, site);
+    }
+};
 
 // Pre-collision deviations of site (x, y) of a staged tile: the same rules
 // as gather_site (free flight, Sec. 4.2 boundaries).  Plane j's window holds
@@ -1253,10 +1341,9 @@ __device__ __forceinline__ void gather_site_smem(const Params& P, const S* box, 
 // The sites of a staged tile that touches a boundary, the obstacle or the
 // probe site, one by one with the boundary rules (kept out of line so that
 // the interior path is allocated registers on its own).
-template <typename S, int EQ, int R, int TX>
+template <typename S, int EQ, int R, int TX, typename Sink>
 __device__ __noinline__ void tma_tile_general(const Params& P, const S* box, int x0, int y0, long long t,
-                                              unsigned* pend_list, unsigned* npend, int pend_cap,
-                                              MlpSlot<EQ>& mslot,
+                                              Sink& sink, MlpSlot<EQ>& mslot,
                                               bool& nonfinite, NewtonCount& nc, bool clean) {
     using L = D2Q9;
     using T = typename Store<S>::T;
@@ -1271,6 +1358,7 @@ __device__ __noinline__ void tma_tile_general(const Params& P, const S* box, int
     for (int s = 0; s < TX / 32; s++) {
         const int x = x0 + lane + 32 * s;
         bool pend = false;
+        T ds = T(-1);
         // the learned form enters with every lane (its warm start is a
         // warp-wide evaluation); lanes outside the grid then carry no site
         if (EQ == EQ_ENERGY_MLP || (x < P.nx && y < P.ny)) {
@@ -1301,13 +1389,18 @@ __device__ __noinline__ void tma_tile_general(const Params& P, const S* box, int
             } else {
                 gather_site_smem<S, R, TX>(P, box, x0, y0, x, y, g);
             }
+            constexpr bool kR = Sink::kResolve;
             if constexpr (EQ == EQ_ENERGY_MLP) {
                 float a0[3];
                 __syncwarp();
                 mlp_site_start<T>(P, mslot.s, fluid, g, a0);
-                if (fluid) pend = update_site<L, T, EQ, Store<S>::kProject>(P, g, x, y, t, nonfinite, nc, a0);
+                if (fluid)
+                    pend = update_site<L, T, EQ, Store<S>::kProject, true, kR>(P, g, x, y, t, nonfinite, nc, a0,
+                                                                               &ds);
             } else {
-                if (fluid) pend = update_site<L, T, EQ, Store<S>::kProject>(P, g, x, y, t, nonfinite, nc);
+                if (fluid)
+                    pend = update_site<L, T, EQ, Store<S>::kProject, true, kR>(P, g, x, y, t, nonfinite, nc,
+                                                                               nullptr, &ds);
             }
             if (inside) {
 #pragma unroll
@@ -1315,19 +1408,50 @@ __device__ __noinline__ void tma_tile_general(const Params& P, const S* box, int
                     Store<S>::store(dst + i * plane + o, 0, fluid ? store_round<L, S>(i, g[i]) : g[i]);
             }
         }
-        warp_pend(P, pend_list, npend, pend_cap, pend, (unsigned)(y * P.nx + x));
+        sink.put(P, pend, ds, (unsigned)(y * P.nx + x));
     }
 }
 
 
+// Exact dS of the pending sites of a clean staged row (warp w: row y; lane
+// l: bit 2 s + h of pmask for column x0 + 2 l + 64 s + h), from the staged
+// planes (the same values the update read) and f* recomputed as the update
+// computed it; the candidates go to bc.  Every lane of the warp calls.
+// Returns what the warp appended.
+template <typename S, int EQ, int R, int TX, int CAP>
+__device__ __noinline__ unsigned resolve_staged_row(const Params& P, const S* box, int x0, int y, unsigned pmask,
+                                                    BlockCandT<CAP>& bc) {
+    using L = D2Q9;
+    using T = typename Store<S>::T;
+    using LY = TmaLayout<S, R, TX>;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const S* sb = box + warp * LY::W + LY::H;
+    unsigned added = 0u;
+#pragma unroll 1
+    for (int b = 0; b < TX / 32; b++) {
+        const int c = 2 * lane + 64 * (b >> 1) + (b & 1);
+        T ds = T(-1);
+        if ((pmask >> b) & 1u) {
+            T g[L::Q], gs[L::Q], rho, ux, uy;
+#pragma unroll
+            for (int i = 0; i < L::Q; i++) g[i] = Store<S>::load(sb + i * LY::PLANE + c - L::cx(i), 0);
+            site_equilibrium<L, T, EQ>(P, g, gs, rho, ux, uy);
+            if (!ghost_column(P, x0 + c)) ds = site_ds<L, T, EQ>(P, g, gs);
+        }
+        added += block_push<T>(P, bc, ds > Par<T>::delta(P), ds, (unsigned)(y * P.nx + x0 + c));
+    }
+    return added;
+}
+
 // One staged tile: rows y0 .. y0 + R - 1 and columns x0 .. x0 + 127 of the
 // run P, from box (the tile's staged source planes); warp w computes row
-// y0 + w, lane l the sites x0 + l + 32 s.  Pending sites (dS not cleared by
-// the bound) are appended to the block's list.
-template <typename S, int EQ, int R, int TX = kTmaTX>
-__device__ __forceinline__ void tma_tile(const Params& P, const S* box, int x0, int y0, long long t,
-                                         unsigned* pend_list, unsigned* npend, int pend_cap, MlpSlot<EQ>& mslot,
-                                         bool& nonfinite, NewtonCount& nc) {
+// y0 + w, lane l the sites x0 + l + 32 s.  The updated sites go to sink.
+// Pc: the parameters for the out-of-line rule-by-rule path (the same values
+// as P, held where that path reads them fast).
+template <typename S, int EQ, int R, int TX = kTmaTX, typename Sink>
+__device__ __forceinline__ void tma_tile(const Params& P, const S* box, int x0, int y0, long long t, Sink& sink,
+                                         MlpSlot<EQ>& mslot, bool& nonfinite, NewtonCount& nc,
+                                         const Params& Pc) {
     using L = D2Q9;
     using T = typename Store<S>::T;
     using LY = TmaLayout<S, R, TX>;
@@ -1348,6 +1472,7 @@ __device__ __forceinline__ void tma_tile(const Params& P, const S* box, int x0, 
     if (clean && !probe_here) {
         const int row = y * nxp + x0;
         const unsigned site0 = (unsigned)(y * P.nx + x0);
+        unsigned pmask = 0u;   // pending sites of the lane (bit 2 s + h: column 2 l + 64 s + h)
         // two adjacent sites per lane, columns c and c + 1 (c = 2 l + 64 s):
         // planes at rest and every store move both with one access, and the
         // two updates are independent work for the scheduler
@@ -1380,12 +1505,22 @@ __device__ __forceinline__ void tma_tile(const Params& P, const S* box, int x0, 
             for (int i = 0; i < L::Q; i++)
                 PairIO<S>::store(dst + i * plane + row + c, store_round<L, S>(i, ga[i]),
                                  store_round<L, S>(i, gb[i]));
-            warp_pend(P, pend_list, npend, pend_cap, pa, site0 + (unsigned)c);
-            warp_pend(P, pend_list, npend, pend_cap, pb, site0 + (unsigned)c + 1u);
+            if constexpr (Sink::kResolve) {
+                pmask |= ((pa ? 1u : 0u) | (pb ? 2u : 0u)) << (2 * s);
+            } else {
+                sink.put(P, pa, T(-1), site0 + (unsigned)c);
+                sink.put(P, pb, T(-1), site0 + (unsigned)c + 1u);
+            }
+        }
+        if constexpr (Sink::kResolve) {
+            // the row's pending sites, from the staged planes (valid until the
+            // next tile's barrier), out of line: the update keeps its registers
+            if (__any_sync(0xffffffffu, pmask != 0u))
+                sink.count += resolve_staged_row<S, EQ, R, TX>(Pc, box, x0, y, pmask, *sink.bc);
         }
         return;
     }
-    tma_tile_general<S, EQ, R, TX>(P, box, x0, y0, t, pend_list, npend, pend_cap, mslot, nonfinite, nc, clean);
+    tma_tile_general<S, EQ, R, TX>(Pc, box, x0, y0, t, sink, mslot, nonfinite, nc, clean);
 }
 // Resident blocks per SM the staged kernel is compiled for: two in general
 // (128 registers per thread with 8-row tiles, 170 with 6-row tiles); three
@@ -1406,15 +1541,16 @@ __global__ void __launch_bounds__(32 * R, tma_min_blocks<S, R, TX>())
     unsigned char* smem = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
     S* stages = reinterpret_cast<S*>(smem);
     unsigned long long* full = reinterpret_cast<unsigned long long*>(smem + STAGES * LY::STAGE_BYTES);
-    constexpr int kPendT = tma_pend_cap<R, TX>();
-    using Shared = TmaShared<kPendT>;
+    constexpr int kCap = tma_cand_cap<R, TX>();
+    constexpr int kRoom = kCap - TX * R;   // what the buffer holds at the top of a tile
+    using Shared = TmaShared<kCap>;
     Shared& sh = *reinterpret_cast<Shared*>(smem + STAGES * LY::STAGE_BYTES + 8 * STAGES);
     constexpr size_t kMlpOff = (STAGES * LY::STAGE_BYTES + 8 * STAGES + sizeof(Shared) + 15) / 16 * 16;
     MlpSlot<EQ>& mslot = *reinterpret_cast<MlpSlot<EQ>*>(smem + kMlpOff);
     if (threadIdx.x == 0) {
         for (int st = 0; st < STAGES; st++) mbar_init(&full[st], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        sh.npend = 0;
+        sh.p = P;
         sh.abort = 0;
         sh.bc.n = 0;
     }
@@ -1424,22 +1560,28 @@ __global__ void __launch_bounds__(32 * R, tma_min_blocks<S, R, TX>())
     const int tiles_x = (P.nx + TX - 1) / TX;
     const int tiles = tiles_x * ((P.ny + R - 1) / R);
 
-    // Tiles are handed out in row-major order by a global counter: thread 0
-    // refills a stage with the tile it claimed at the previous refill and
-    // claims the next one (the atomic's latency then overlaps a tile's
-    // computation), and publishes the tile's index with the stage's mbarrier
-    // (-1: none left; the phase is then completed by a plain arrive, without
-    // a copy).
-    int next_tile = 0;
+    // Tiles are handed out by a global counter, claim c taking tile
+    // tile_order[c] (boundary tiles first) or c: thread 0 refills a stage
+    // with the tile it claimed at the previous refill and claims the next
+    // one (the latencies of the atomic and of the order entry then overlap a
+    // tile's computation), and publishes the tile's index with the stage's
+    // mbarrier (-1: none left; the phase is then completed by a plain
+    // arrive, without a copy).
+    int next_claim = 0, next_tile = 0;
+    auto claim = [&]() {
+        next_claim = (int)atomicAdd(P.tile_counter, 1u);
+        next_tile = next_claim;
+        if (P.tile_order && next_claim < tiles) next_tile = __ldg(P.tile_order + next_claim);
+    };
     auto fill = [&](int st) {
         unsigned long long* bar = &full[st];
-        const int tile = next_tile;
-        if (tile >= tiles) {
+        if (next_claim >= tiles) {
             sh.tile[st] = -1;
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
             return;
         }
-        next_tile = (int)atomicAdd(P.tile_counter, 1u);
+        const int tile = next_tile;
+        claim();
         sh.tile[st] = tile;
         const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
         mbar_expect_tx(bar, (unsigned)LY::TX_BYTES);
@@ -1451,35 +1593,38 @@ __global__ void __launch_bounds__(32 * R, tma_min_blocks<S, R, TX>())
     if (threadIdx.x == 0) {
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<unsigned long long>(&tm))
                      : "memory");
-        next_tile = (int)atomicAdd(P.tile_counter, 1u);
+        claim();
         for (int st = 0; st < STAGES - 1; st++) fill(st);
     }
     bool nonfinite = false;
     NewtonCount nc = {0, 0, 0, 0};
+    // The sites the dS bound does not clear are resolved as they are
+    // updated; the candidates go to the block's buffer, which the block cuts
+    // to its k best between tiles.  A cut happens once some warp appended
+    // more than its share (1 / R) of the room above what a cut keeps: the
+    // buffer then never holds more than kRoom entries at the top of a tile,
+    // and one tile adds at most TX * R.
+    const int kept = P.k > 0 && P.k < kRoom ? P.k : 0;
+    const unsigned share = (unsigned)((kRoom - kept) / R);
+    CandSink<kCap> sink{&sh.bc, 0u};
     int jj = 0;
     for (;; jj++) {
         const int st = jj % STAGES;
         const unsigned parity = (unsigned)((jj / STAGES) & 1);
-        // every thread waits; a wait that gave up anywhere ends the block's
-        // loop everywhere (the vote keeps the barriers matched)
-        if (__syncthreads_or(!mbar_wait(&full[st], parity))) {
-            if (threadIdx.x == 0) {
-                atomicOr(P.err, ERR_TIMEOUT);
-                sh.abort = 1;
+        // every thread waits.  One vote decides, for every warp at once, to
+        // stop (a wait that gave up anywhere: abort is written before the
+        // barrier only) or to cut the candidates (a warp's count is its own),
+        // so that the barriers stay matched
+        const bool ok = mbar_wait(&full[st], parity);
+        if (!ok) sh.abort = 1;
+        if (__syncthreads_or(!ok || sink.count > share)) {
+            if (sh.abort) {
+                if (threadIdx.x == 0) atomicOr(P.err, ERR_TIMEOUT);
+                break;
             }
-            break;
-        }
-        // resolve the block's pending sites once its list could not take
-        // another tile's, so that none overflow to the global list (which the
-        // last block alone would resolve).  npend is read after the barrier
-        // above, with no writes to it until the next tile: the branch is
-        // uniform.
-        if (sh.npend > (unsigned)(kPendT - TX * R)) {
-            resolve_list<L, S, EQ>(P, (int)min(sh.npend, (unsigned)kPendT),
-                                   [&](int j) { return sh.pend[j]; }, &sh.bc, &sh.ss.sc);
-            __syncthreads();
-            if (threadIdx.x == 0) sh.npend = 0;
-            __syncthreads();
+            if (P.k < kRoom) block_cut(sh.bc, sh.ss.sc, P.k);
+            else block_flush(sh.p, sh.bc);
+            sink.count = 0;
         }
         const int tile = sh.tile[st];
         if (tile < 0) break;
@@ -1492,7 +1637,7 @@ __global__ void __launch_bounds__(32 * R, tma_min_blocks<S, R, TX>())
         }
         const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
         const S* box = stages + (size_t)st * (LY::STAGE_BYTES / sizeof(S));
-        tma_tile<S, EQ, R, TX>(P, box, tx * TX, ty * R, t, sh.pend, &sh.npend, kPendT, mslot, nonfinite, nc);
+        tma_tile<S, EQ, R, TX>(P, box, tx * TX, ty * R, t, sink, mslot, nonfinite, nc, sh.p);
     }
     __syncthreads();
     if (sh.abort && threadIdx.x == 0) {
@@ -1510,7 +1655,7 @@ __global__ void __launch_bounds__(32 * R, tma_min_blocks<S, R, TX>())
     const int scap = (int)min((size_t)kStage, (size_t)STAGES * LY::STAGE_BYTES / 12);
     unsigned long long* skey = reinterpret_cast<unsigned long long*>(smem);
     unsigned* sidx = reinterpret_cast<unsigned*>(smem + 8 * scap);
-    finish_parts<L, S, EQ>(P, sh.pend, sh.npend, kPendT, sh.is_last, sh.ss, sh.bc, skey, sidx, scap);
+    finish_parts<L, S, EQ>(sh.p, nullptr, 0u, 0, sh.is_last, sh.ss, sh.bc, skey, sidx, scap);
 }
 
 // ---------------------------------------------------------------------------
