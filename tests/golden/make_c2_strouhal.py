@@ -4,7 +4,7 @@ face at 5L, polynomial f*, free-slip walls, zero-gradient outflow,
 u_inf = 0.05 with seeded 1e-4 inflow noise, Re = 1000, delta = 1e-3, k = 16),
 2e5 steps, probe at (4L, -2L) from the cylinder centre (Sec. 4.2.1), St from
 the final quarter (the oracle's own estimator).  Uses the oracle only; takes
-about half an hour on eight host cores.
+about an hour on eight host cores.
 
     python tests/golden/make_c2_strouhal.py
 """
