@@ -330,26 +330,38 @@ int encode_tensor_map(const lb_handle* h, int b, int rows, int cols, CUtensorMap
     return LB_OK;
 }
 
-// Claim order of the staged tiles (rows x cols sites): the tiles that take
-// the rule-by-rule path (the grid's edge rows and columns, the obstacle and
-// its neighbours; the same test as the kernel's) first, row-major, then the
-// interior tiles, row-major.  The slow tiles then run while every block is
-// busy, and the last tiles handed out are interior tiles of equal cost.
+// Claim order of the staged tiles (rows x cols sites).  The tiles that take
+// the rule-by-rule path (the grid's first and last rows, a ragged last
+// column of tiles, the obstacle and its neighbours; the same test as the
+// kernel's, whose columns x = 0 and x = nx - 1 go apart) cost several times an
+// interior tile: they are spread evenly over the first three quarters of
+// the claims, where they overlap interior tiles that keep the memory busy,
+// and the last claims are interior tiles of equal cost, so that the blocks
+// run out of work together.  Both kinds keep their row-major order.
 std::vector<int> staged_tile_order(const lb_handle* h, int rows, int cols) {
     const int tiles_x = (h->nx + cols - 1) / cols, tiles_y = (h->ny + rows - 1) / rows;
     const lb_boundaries& b = h->bc;
+    std::vector<int> slow, fast;
+    for (int ty = 0; ty < tiles_y; ty++)
+        for (int tx = 0; tx < tiles_x; tx++) {
+            const int x0 = tx * cols, y0 = ty * rows;
+            const bool clean = x0 + cols <= h->nx && y0 >= 1 && y0 + rows <= h->ny - 1 &&
+                               (b.obstacle_w == 0 || x0 + cols + 1 <= b.obstacle_x0 ||
+                                x0 - 1 >= b.obstacle_x0 + b.obstacle_w || y0 + rows + 1 <= b.obstacle_y0 ||
+                                y0 - 1 >= b.obstacle_y0 + b.obstacle_h);
+            (clean ? fast : slow).push_back(ty * tiles_x + tx);
+        }
+    const size_t n = slow.size() + fast.size();
+    const size_t span = std::max(slow.size(), n * 3 / 4);   // claims the slow tiles are spread over
     std::vector<int> order;
-    order.reserve((size_t)tiles_x * tiles_y);
-    for (int pass = 0; pass < 2; pass++)
-        for (int ty = 0; ty < tiles_y; ty++)
-            for (int tx = 0; tx < tiles_x; tx++) {
-                const int x0 = tx * cols, y0 = ty * rows;
-                const bool clean = x0 >= 1 && x0 + cols <= h->nx - 1 && y0 >= 1 && y0 + rows <= h->ny - 1 &&
-                                   (b.obstacle_w == 0 || x0 + cols + 1 <= b.obstacle_x0 ||
-                                    x0 - 1 >= b.obstacle_x0 + b.obstacle_w || y0 + rows + 1 <= b.obstacle_y0 ||
-                                    y0 - 1 >= b.obstacle_y0 + b.obstacle_h);
-                if (clean == (pass == 1)) order.push_back(ty * tiles_x + tx);
-            }
+    order.reserve(n);
+    size_t js = 0, jf = 0;
+    for (size_t c = 0; c < n; c++) {
+        // slow tile j goes to claim floor(j * span / nslow)
+        const bool take_slow = js < slow.size() && c >= js * span / slow.size();
+        if (take_slow || jf == fast.size()) order.push_back(slow[js++]);
+        else order.push_back(fast[jf++]);
+    }
     return order;
 }
 

@@ -1341,7 +1341,7 @@ __device__ __forceinline__ void gather_site_smem(const Params& P, const S* box, 
 // The sites of a staged tile that touches a boundary, the obstacle or the
 // probe site, one by one with the boundary rules (kept out of line so that
 // the interior path is allocated registers on its own).
-template <typename S, int EQ, int R, int TX, typename Sink>
+template <typename S, int EQ, int R, int TX, bool SPLIT, typename Sink>
 __device__ __noinline__ void tma_tile_general(const Params& P, const S* box, int x0, int y0, long long t,
                                               Sink& sink, MlpSlot<EQ>& mslot,
                                               bool& nonfinite, NewtonCount& nc, bool clean) {
@@ -1361,8 +1361,10 @@ __device__ __noinline__ void tma_tile_general(const Params& P, const S* box, int
         T ds = T(-1);
         // the learned form enters with every lane (its warm start is a
         // warp-wide evaluation); lanes outside the grid then carry no site
-        if (EQ == EQ_ENERGY_MLP || (x < P.nx && y < P.ny)) {
-            const bool inside = x < P.nx && y < P.ny;
+        // SPLIT: the columns x = 0 and x = nx - 1 are updated apart (edge_item)
+        const bool mine = x < P.nx && y < P.ny && !(SPLIT && (x == 0 || x == P.nx - 1));
+        if (EQ == EQ_ENERGY_MLP || mine) {
+            const bool inside = mine;
             const int c = x - x0;
             const int o = y * nxp + x;
             bool shift = clean;
@@ -1413,6 +1415,51 @@ __device__ __noinline__ void tma_tile_general(const Params& P, const S* box, int
 }
 
 
+// The columns x = 0 and x = nx - 1 of the grid (the sites whose sources
+// leave the grid in x), apart from the staged tiles: edge item e covers
+// sites e * 32 R .. (e + 1) * 32 R - 1 of the list x = 0 (rows 0 .. ny - 1)
+// then x = nx - 1, one site per lane, gathered from the source field with
+// the boundary rules (gather_site).  Every lane of the block calls.
+template <typename S, int EQ, int R, typename Sink>
+__device__ __noinline__ void edge_item(const Params& P, int item, long long t, Sink& sink, MlpSlot<EQ>& mslot,
+                                       bool& nonfinite, NewtonCount& nc) {
+    using L = D2Q9;
+    using T = typename Store<S>::T;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ncols = P.nx > 1 ? 2 : 1;
+    const int e = (item * R + warp) * 32 + lane;
+    const bool inside = e < ncols * P.ny;
+    const int x = inside && e >= P.ny ? P.nx - 1 : 0;
+    const int y = inside ? (e >= P.ny ? e - P.ny : e) : 0;
+    const bool fluid = inside && !is_solid(P, x, y);
+    T g[L::Q];
+    if (fluid) {
+        gather_site<L, S>(P, x, y, g);
+    } else {
+#pragma unroll
+        for (int i = 0; i < L::Q; i++) g[i] = T(0);
+    }
+    bool pend = false;
+    T ds = T(-1);
+    constexpr bool kR = Sink::kResolve;
+    if constexpr (EQ == EQ_ENERGY_MLP) {
+        float a0[3];
+        mlp_site_start<T>(P, mslot.s, fluid, g, a0);
+        if (fluid) pend = update_site<L, T, EQ, Store<S>::kProject, true, kR>(P, g, x, y, t, nonfinite, nc, a0, &ds);
+    } else {
+        if (fluid)
+            pend = update_site<L, T, EQ, Store<S>::kProject, true, kR>(P, g, x, y, t, nonfinite, nc, nullptr, &ds);
+    }
+    if (inside) {
+        S* dst = static_cast<S*>(P.dst);
+        const long long o = (long long)y * P.nxp + x;
+#pragma unroll
+        for (int i = 0; i < L::Q; i++)
+            Store<S>::store(dst, i * P.plane + o, fluid ? store_round<L, S>(i, g[i]) : g[i]);
+    }
+    sink.put(P, pend, ds, (unsigned)(y * P.nx + x));
+}
+
 // Exact dS of the pending sites of a clean staged row (warp w: row y; lane
 // l: bit 2 s + h of pmask for column x0 + 2 l + 64 s + h), from the staged
 // planes (the same values the update read) and f* recomputed as the update
@@ -1448,7 +1495,11 @@ __device__ __noinline__ unsigned resolve_staged_row(const Params& P, const S* bo
 // y0 + w, lane l the sites x0 + l + 32 s.  The updated sites go to sink.
 // Pc: the parameters for the out-of-line rule-by-rule path (the same values
 // as P, held where that path reads them fast).
-template <typename S, int EQ, int R, int TX = kTmaTX, typename Sink>
+// SPLIT: the columns x = 0 and x = nx - 1 are not updated here (edge_item
+// updates them); a tile then takes the interior path whenever it spans TX
+// columns of the grid and its rows and columns stay away from the y sides
+// and the obstacle.
+template <typename S, int EQ, int R, int TX = kTmaTX, bool SPLIT = false, typename Sink>
 __device__ __forceinline__ void tma_tile(const Params& P, const S* box, int x0, int y0, long long t, Sink& sink,
                                          MlpSlot<EQ>& mslot, bool& nonfinite, NewtonCount& nc,
                                          const Params& Pc) {
@@ -1459,8 +1510,8 @@ __device__ __forceinline__ void tma_tile(const Params& P, const S* box, int x0, 
     S* __restrict__ dst = static_cast<S*>(P.dst);
     const int nxp = P.nxp, plane = (int)P.plane;
     const int y = y0 + warp;
-    const bool clean = !P.prestream && x0 >= 1 && x0 + TX <= P.nx - 1 && y0 >= 1 &&
-                       y0 + R <= P.ny - 1 &&
+    const bool xin = SPLIT ? x0 + TX <= P.nx : x0 >= 1 && x0 + TX <= P.nx - 1;
+    const bool clean = !P.prestream && xin && y0 >= 1 && y0 + R <= P.ny - 1 &&
                        (P.ow == 0 || x0 + TX + 1 <= P.ox0 || x0 - 1 >= P.ox0 + P.ow ||
                         y0 + R + 1 <= P.oy0 || y0 - 1 >= P.oy0 + P.oh);
     const S* sb = box + warp * LY::W + LY::H;
@@ -1490,6 +1541,21 @@ __device__ __forceinline__ void tma_tile(const Params& P, const S* box, int x0, 
                     gb[i] = Store<S>::load(q + 1 - L::cx(i), 0);
                 }
             }
+            // SPLIT: a site of column 0 or nx - 1 (lane 0 or 31 of an edge
+            // tile) is left to edge_item; it is updated here from the rest
+            // state at unit density (whatever the staged halo holds) and is
+            // neither stored nor pending
+            bool ea = false, eb = false;
+            if constexpr (SPLIT) {
+                ea = x0 + c == 0 || x0 + c == P.nx - 1;
+                eb = x0 + c + 1 == P.nx - 1;
+                const T r1 = T(1) - Par<T>::rho0(P);
+#pragma unroll
+                for (int i = 0; i < L::Q; i++) {
+                    ga[i] = ea ? T(L::w(i)) * r1 : ga[i];
+                    gb[i] = eb ? T(L::w(i)) * r1 : gb[i];
+                }
+            }
             bool pa, pb;
             if constexpr (EQ == EQ_ENERGY_MLP) {
                 float a0[3];
@@ -1501,10 +1567,20 @@ __device__ __forceinline__ void tma_tile(const Params& P, const S* box, int x0, 
                 pa = update_site<L, T, EQ, Store<S>::kProject, false>(P, ga, x0 + c, y, t, nonfinite, nc);
                 pb = update_site<L, T, EQ, Store<S>::kProject, false>(P, gb, x0 + c + 1, y, t, nonfinite, nc);
             }
+            if (!(ea | eb)) {
 #pragma unroll
-            for (int i = 0; i < L::Q; i++)
-                PairIO<S>::store(dst + i * plane + row + c, store_round<L, S>(i, ga[i]),
-                                 store_round<L, S>(i, gb[i]));
+                for (int i = 0; i < L::Q; i++)
+                    PairIO<S>::store(dst + i * plane + row + c, store_round<L, S>(i, ga[i]),
+                                     store_round<L, S>(i, gb[i]));
+            } else {
+#pragma unroll
+                for (int i = 0; i < L::Q; i++) {
+                    if (!ea) Store<S>::store(dst + i * plane + row + c, 0, store_round<L, S>(i, ga[i]));
+                    if (!eb) Store<S>::store(dst + i * plane + row + c + 1, 0, store_round<L, S>(i, gb[i]));
+                }
+            }
+            pa = pa && !ea;
+            pb = pb && !eb;
             if constexpr (Sink::kResolve) {
                 pmask |= ((pa ? 1u : 0u) | (pb ? 2u : 0u)) << (2 * s);
             } else {
@@ -1520,7 +1596,7 @@ __device__ __forceinline__ void tma_tile(const Params& P, const S* box, int x0, 
         }
         return;
     }
-    tma_tile_general<S, EQ, R, TX>(Pc, box, x0, y0, t, sink, mslot, nonfinite, nc, clean);
+    tma_tile_general<S, EQ, R, TX, SPLIT>(Pc, box, x0, y0, t, sink, mslot, nonfinite, nc, clean);
 }
 // Resident blocks per SM the staged kernel is compiled for: two in general
 // (128 registers per thread with 8-row tiles, 170 with 6-row tiles); three
@@ -1559,24 +1635,31 @@ __global__ void __launch_bounds__(32 * R, tma_min_blocks<S, R, TX>())
     const long long t = *P.step;
     const int tiles_x = (P.nx + TX - 1) / TX;
     const int tiles = tiles_x * ((P.ny + R - 1) / R);
+    // the x = 0 and x = nx - 1 columns go first, as edge items of 32 R sites
+    const int edge_items = ((P.nx > 1 ? 2 : 1) * P.ny + 32 * R - 1) / (32 * R);
+    const int claims = edge_items + tiles;
 
-    // Tiles are handed out by a global counter, claim c taking tile
-    // tile_order[c] (boundary tiles first) or c: thread 0 refills a stage
-    // with the tile it claimed at the previous refill and claims the next
-    // one (the latencies of the atomic and of the order entry then overlap a
-    // tile's computation), and publishes the tile's index with the stage's
-    // mbarrier (-1: none left; the phase is then completed by a plain
-    // arrive, without a copy).
+    // Work is handed out by a global counter: claim c < edge_items is edge
+    // item c, the others tile tile_order[c - edge_items] (boundary tiles
+    // spread over the first claims) or c - edge_items.  Thread 0 refills a
+    // stage with the work it claimed at the previous refill and claims the
+    // next (the latencies of the atomic and of the order entry then overlap
+    // a tile's computation), and publishes it with the stage's mbarrier:
+    // the tile's index, -2 - e for edge item e, -1 when none is left (the
+    // phase is then completed by a plain arrive, without a copy, as for an
+    // edge item).
     int next_claim = 0, next_tile = 0;
     auto claim = [&]() {
         next_claim = (int)atomicAdd(P.tile_counter, 1u);
-        next_tile = next_claim;
-        if (P.tile_order && next_claim < tiles) next_tile = __ldg(P.tile_order + next_claim);
+        const int c = next_claim - edge_items;
+        next_tile = c < 0 ? -2 - next_claim : c;
+        if (P.tile_order && c >= 0 && c < tiles) next_tile = __ldg(P.tile_order + c);
     };
     auto fill = [&](int st) {
         unsigned long long* bar = &full[st];
-        if (next_claim >= tiles) {
-            sh.tile[st] = -1;
+        if (next_claim >= claims || next_tile < 0) {
+            sh.tile[st] = next_claim >= claims ? -1 : next_tile;
+            if (next_claim < claims) claim();
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
             return;
         }
@@ -1627,7 +1710,7 @@ __global__ void __launch_bounds__(32 * R, tma_min_blocks<S, R, TX>())
             sink.count = 0;
         }
         const int tile = sh.tile[st];
-        if (tile < 0) break;
+        if (tile == -1) break;
         if (threadIdx.x == 0) {
             // the stage being refilled was last read in iteration jj - 1,
             // whose reads the barrier at the top of this iteration ordered
@@ -1635,9 +1718,13 @@ __global__ void __launch_bounds__(32 * R, tma_min_blocks<S, R, TX>())
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             fill((jj + STAGES - 1) % STAGES);
         }
+        if (tile <= -2) {
+            edge_item<S, EQ, R>(sh.p, -2 - tile, t, sink, mslot, nonfinite, nc);
+            continue;
+        }
         const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
         const S* box = stages + (size_t)st * (LY::STAGE_BYTES / sizeof(S));
-        tma_tile<S, EQ, R, TX>(P, box, tx * TX, ty * R, t, sink, mslot, nonfinite, nc, sh.p);
+        tma_tile<S, EQ, R, TX, true>(P, box, tx * TX, ty * R, t, sink, mslot, nonfinite, nc, sh.p);
     }
     __syncthreads();
     if (sh.abort && threadIdx.x == 0) {
