@@ -1630,6 +1630,15 @@ __global__ void __launch_bounds__(32 * R, tma_min_blocks<S, R, TX>())
         sh.abort = 0;
         sh.bc.n = 0;
     }
+    // Launched as a programmatic dependent of the previous kernel in the
+    // stream: the block may start while that kernel finishes, and the code
+    // above reads only the launch's parameters and writes only shared
+    // memory.  Every thread waits here until the previous kernel has
+    // completed and its writes are visible, then lets the next kernel of the
+    // stream start its blocks as this one's leave the SMs (they wait here in
+    // turn).
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     mslot.fill(P);
     __syncthreads();
     const long long t = *P.step;
@@ -2012,9 +2021,21 @@ cudaError_t launch_d2q9_tma(const Params& P, const void* tmap, cudaStream_t st) 
     const long long tiles = (long long)((P.nx + TX - 1) / TX) * ((P.ny + R - 1) / R);
     const long long want = tiles;   // at least one tile per block
     const unsigned blocks = (unsigned)std::max(1ll, std::min(want, (long long)P.grid_blocks));
-    k_collide_d2q9_tma<S, EQ, R, STAGES, TX><<<blocks, 32 * R, smem, st>>>(
-        P, *static_cast<const CUtensorMap*>(tmap));
-    return cudaGetLastError();
+    // programmatic stream serialisation: the launch may begin before the
+    // previous kernel in the stream completes (the kernel waits for it with
+    // griddepcontrol.wait before touching device memory)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(32 * R);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_collide_d2q9_tma<S, EQ, R, STAGES, TX>, P,
+                              *static_cast<const CUtensorMap*>(tmap));
 }
 
 template <typename S, int EQ, int R, int STAGES, int TX = kTmaTX>
