@@ -505,10 +505,17 @@ def batched_form(args, stream, peaks, world=1, rank=0):
         cache = args.autotune_cache or os.path.join(tempfile.gettempdir(),
                                                     "lbm_gb300_autotune_rank%d.json" % rank)
         t0 = time.perf_counter()
-        v = b.autotune(steps=10, cache_path=cache)
+        v = b.autotune(steps=96, cache_path=cache)
         info = b.info()
         out.update({"runs": len(ws_all), "sites": total_sites, "runs_rank0": info["runs"],
                     "autotuned_variant": v, "autotune_s": round(time.perf_counter() - t0, 3)})
+        try:
+            with open(cache) as fh:
+                entries = list(json.load(fh).values())
+            if len(entries) == 1:   # a fresh cache: this batch's timings of every variant
+                out["autotune_ms_per_step"] = entries[0].get("ms_per_step")
+        except (OSError, ValueError, AttributeError):
+            pass
 
         def timed(fn, n):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

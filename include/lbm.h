@@ -336,8 +336,8 @@ int lb_kernel_times(lb_handle* h, double* collide_ms, long long* collide_launche
  * Shared-memory-staged shapes (tensor-memory-accelerator copies, for every
  * population plane, of the R rows of the R x C-site block tile's sources in
  * that plane plus 16 bytes of halo columns; R rows, C columns, STAGES tiles
- * in flight per block): 4 = 8 x 128, STAGES 2 (default of FP64 and FP16
- * storage);  5 = 6 x 128, STAGES 3 (default of FP32 storage, plain and
+ * in flight per block): 4 = 8 x 128, STAGES 2 (default of FP64 storage);
+ * 5 = 6 x 128, STAGES 3 (default of FP32 and FP16 storage, plain and
  * deviation);  6 = 8 x 64, STAGES 2 (three blocks per SM).  The
  * energy-constrained forms are built for shapes 0 (1, 8, 2: 128 registers
  * per thread), 1 (2 and 3 run 1), 4 and 5, and refuse 6 (LB_ERR_ARG); their
@@ -476,8 +476,10 @@ int lb_batch_autotune(lb_batch* b, int steps, const char* cache_path, int* varia
 int lb_batch_set_timing(lb_batch* b, int enable);
 int lb_batch_kernel_times(lb_batch* b, double* ms, long long* launches, int reset);
 
-/* out[8]: runs, sites, tiles, grid blocks, blocks per SM, variant, tile
- * rows, steps per graph. */
+/* out[8]: runs, sites, work items of the batched kernel (each run's tiles,
+ * plus its edge items: the x = 0 and x = nx - 1 columns, 32 x tile rows
+ * sites each), grid blocks, blocks per SM, variant, tile rows, steps per
+ * graph. */
 int lb_batch_info(lb_batch* b, long long* out);
 
 #ifdef __cplusplus

@@ -44,10 +44,11 @@ int fail(int code, const char* fmt, ...) {
 
 constexpr int kGraphSteps = 32;      // steps per captured graph (even: buffers return)
 constexpr int kDefaultLog = 65536;
-// Default tile shapes, the fastest measured on GB300: FP32 storage (plain
-// and deviation) stages 6-row tiles with 2 more in flight per block (shape
-// 5); FP16 and FP64 storage 8-row tiles with 1 more (shape 4; FP16 with
-// three blocks per SM).  The energy forms are bound by the Newton solve, not
+// Default tile shapes, the fastest measured on GB300: FP32 and FP16 storage
+// (plain and deviation) stage 6-row tiles with 2 more in flight per block
+// (shape 5; FP16 at 1000 steps of the 4096 x 2048 cylinder: 90.8 k MLUPS
+// against 86.8 k with 8-row tiles at three blocks per SM); FP64 storage
+// 8-row tiles with 1 more (shape 4).  The energy forms are bound by the Newton solve, not
 // by memory: FP64 storage's FP64 finish wants the most resident warps
 // (register-fed shape 1); the float-float finish of FP32 / FP16 storage and
 // the network's warm start run best in the staged shape 4 (measured at
@@ -55,7 +56,7 @@ constexpr int kDefaultLog = 65536;
 // on shape 5; warm start 0.35 against 0.54 and 0.35).
 int default_tile_shape(int lattice, int eq, int precision) {
     if (lattice != LB_D2Q9) return 0;
-    if (eq < LB_EQ_ENTROPIC_ENERGY) return (precision == LB_F32 || precision == LB_F32_DEV) ? 5 : 4;
+    if (eq < LB_EQ_ENTROPIC_ENERGY) return precision == LB_F64 ? 4 : 5;
     if (precision == LB_F64) return 1;
     return 4;
 }

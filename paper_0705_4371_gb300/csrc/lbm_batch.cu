@@ -102,7 +102,10 @@ int configure(lb_batch* b) {
     std::vector<int> base(n + 1, 0);
     for (int r = 0; r < n; r++) {
         const lb_run_desc& d = b->desc[r];
-        const long long t = (long long)((d.nx + 127) / 128) * ((d.ny + b->rows - 1) / b->rows);
+        // work items of the run: its edge items (the x = 0 and x = nx - 1
+        // columns, 32 x rows sites each) and its tiles
+        const long long edge = ((long long)(d.nx > 1 ? 2 : 1) * d.ny + 32 * b->rows - 1) / (32 * b->rows);
+        const long long t = edge + (long long)((d.nx + 127) / 128) * ((d.ny + b->rows - 1) / b->rows);
         if (base[r] + t > 0x7fffffffll) return fail(LB_ERR_ARG, "too many tiles in the batch");
         base[r + 1] = base[r] + (int)t;
     }

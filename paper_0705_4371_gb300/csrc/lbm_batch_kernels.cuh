@@ -101,10 +101,20 @@ __global__ void __launch_bounds__(32 * R, 16 / R) k_collide_batch(const __grid_c
         for (int k = 0; k < (int)(sizeof(Params) / 8); k++) w[k] = __ldg(src + k);
 #pragma unroll
         for (int k = 0; k < (int)(sizeof(Params) / 8); k++) dst[k] = w[k];
-        const int lt = tile - tile_base[lo];
-        sh.tile[st] = lt;
+        // a run's work: its edge items (the x = 0 and x = nx - 1 columns,
+        // 32 R sites each), then its tiles
+        const int nx = sp[st].nx, ny = sp[st].ny;
+        const int edge_items = ((nx > 1 ? 2 : 1) * ny + 32 * R - 1) / (32 * R);
+        int lt = tile - tile_base[lo];
         sh.run[st] = lo;
-        const int tiles_x = (sp[st].nx + TX - 1) / TX;
+        if (lt < edge_items) {
+            sh.tile[st] = -2 - lt;
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+            return;
+        }
+        lt -= edge_items;
+        sh.tile[st] = lt;
+        const int tiles_x = (nx + TX - 1) / TX;
         const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
         mbar_expect_tx(bar, (unsigned)LY::TX_BYTES);
         S* base = stages + (size_t)st * (LY::STAGE_BYTES / sizeof(S));
@@ -126,7 +136,7 @@ __global__ void __launch_bounds__(32 * R, 16 / R) k_collide_batch(const __grid_c
             break;
         }
         const int lt = sh.tile[st];
-        if (lt < 0) break;
+        if (lt == -1) break;
         const int r = sh.run[st];
         if (threadIdx.x == 0) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -140,7 +150,8 @@ __global__ void __launch_bounds__(32 * R, 16 / R) k_collide_batch(const __grid_c
         NewtonCount nc = {0, 0, 0, 0};
         const S* box = stages + (size_t)st * (LY::STAGE_BYTES / sizeof(S));
         PendSink sink{sh.pend, &sh.npend, kPend};
-        tma_tile<S, EQ, R>(P, box, tx * TX, ty * R, t, sink, mslot, nonfinite, nc, P);
+        if (lt <= -2) edge_item<S, EQ, R>(P, -2 - lt, t, sink, mslot, nonfinite, nc);
+        else tma_tile<S, EQ, R, kTmaTX, true>(P, box, tx * TX, ty * R, t, sink, mslot, nonfinite, nc, P);
         const int nf = __syncthreads_or(nonfinite);
         // the tile's pending sites (npend is read between barriers: uniform)
         if (sh.npend > 0) {

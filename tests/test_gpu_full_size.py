@@ -31,7 +31,7 @@ def lbm():
 def _spun_up(lbm, w, prec):
     g = lbm.Lattice.from_workload(w, precision=lbm.PRECISIONS[prec])
     # the default shape, the one the benchmark times
-    assert g.info()["tile_shape"] == (5 if prec in ("f32", "f32dev") else 4)
+    assert g.info()["tile_shape"] == (4 if prec == "f64" else 5)
     g.init_equilibrium(*inputs.cylinder_fields(w, noise=1e-2))
     g.step(SPIN_UP)
     g.sync()
