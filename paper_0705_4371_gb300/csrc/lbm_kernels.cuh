@@ -1524,6 +1524,7 @@ __device__ __forceinline__ void tma_tile(const Params& P, const S* box, int x0, 
         const int row = y * nxp + x0;
         const unsigned site0 = (unsigned)(y * P.nx + x0);
         unsigned pmask = 0u;   // pending sites of the lane (bit 2 s + h: column 2 l + 64 s + h)
+        const bool edge_tile = SPLIT && (x0 == 0 || x0 + TX >= P.nx - 1);
         // two adjacent sites per lane, columns c and c + 1 (c = 2 l + 64 s):
         // planes at rest and every store move both with one access, and the
         // two updates are independent work for the scheduler
@@ -1547,13 +1548,15 @@ __device__ __forceinline__ void tma_tile(const Params& P, const S* box, int x0, 
             // neither stored nor pending
             bool ea = false, eb = false;
             if constexpr (SPLIT) {
-                ea = x0 + c == 0 || x0 + c == P.nx - 1;
-                eb = x0 + c + 1 == P.nx - 1;
-                const T r1 = T(1) - Par<T>::rho0(P);
+                if (edge_tile) {   // uniform: only the tiles at either end of the rows
+                    ea = x0 + c == 0 || x0 + c == P.nx - 1;
+                    eb = x0 + c + 1 == P.nx - 1;
+                    const T r1 = T(1) - Par<T>::rho0(P);
 #pragma unroll
-                for (int i = 0; i < L::Q; i++) {
-                    ga[i] = ea ? T(L::w(i)) * r1 : ga[i];
-                    gb[i] = eb ? T(L::w(i)) * r1 : gb[i];
+                    for (int i = 0; i < L::Q; i++) {
+                        ga[i] = ea ? T(L::w(i)) * r1 : ga[i];
+                        gb[i] = eb ? T(L::w(i)) * r1 : gb[i];
+                    }
                 }
             }
             bool pa, pb;

@@ -108,3 +108,19 @@ def test_c2_re1000_probe_follows_the_oracle_trajectory(lbm):
     err = np.abs(got - ref).max() / w.u_in[0]
     print("c2 Re 1000 FP64 probe, 2e4 steps: max |du| / u_inf = %.2e" % err)
     assert err <= 1e-8
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_c2_re150_strouhal_matches_the_oracle_run(lbm, prec):
+    # The same channel at Re = 150, where the wake sheds periodically: the
+    # Strouhal number of the GPU's free run of 1e5 steps (seeded 1e-2 inflow
+    # noise) against the FP64 oracle's (tests/golden/c2_re150_strouhal.txt),
+    # within 1 %
+    from paper_0705_4371_gb300 import experiments
+    st_o = float(_golden("c2_re150_strouhal.txt")[0])
+    w = inputs.workload_c2(150.0)
+    r = experiments.cylinder_run(w, 100000, precision=lbm.PRECISIONS[prec], noise=1e-2, chunk=20000)
+    assert r["diverged_at"] is None
+    print("c2 Re 150 Strouhal %s: GPU %.5f oracle %.5f (%.3f %%)"
+          % (prec, r["strouhal"], st_o, 100 * abs(r["strouhal"] - st_o) / st_o))
+    assert abs(r["strouhal"] - st_o) <= 0.01 * st_o
