@@ -614,9 +614,14 @@ __device__ __noinline__ void select_and_fix(const Params& P, SelectShared& ss,
                                             int stage_cap, int mode) {
     using T = typename Store<S>::T;
     const int tid = threadIdx.x, nt = blockDim.x;
-    const long long t = __ldcg(P.step);
-    const long long r = t - P.replay_t0;
-    const bool replay = P.replay_cnt && r >= 0 && r < P.replay_n;
+    const long long t = __ldcg(P.step);   // used at the end: its latency overlaps the selection
+    long long r = 0;
+    bool replay = false;
+    if (P.replay_cnt) {
+        r = t - P.replay_t0;
+        replay = r >= 0 && r < P.replay_n;
+    }
+    int mine = -1;   // the site this thread selected itself, when it did (j = tid)
     if (replay) {
         const int c = P.replay_cnt[r];
         const long long off = P.replay_off[r];
@@ -628,7 +633,9 @@ __device__ __noinline__ void select_and_fix(const Params& P, SelectShared& ss,
         const int n = (int)__ldcg(P.cand_count);
         if (n <= P.k) {
             for (int j = tid; j < n; j += nt) {
-                P.sel_idx[j] = (int)__ldcg(P.cand_idx + j);
+                const int id = (int)__ldcg(P.cand_idx + j);
+                P.sel_idx[j] = id;
+                if (j == tid) mine = id;
                 if (P.sel_key) P.sel_key[j] = __ldcg(P.cand_key + j);
             }
             if (tid == 0) ss.nsel = n;
@@ -665,7 +672,7 @@ __device__ __noinline__ void select_and_fix(const Params& P, SelectShared& ss,
     if (mode == 0) {
         const long long nsites = (long long)P.nx * P.ny;
         for (int j = tid; j < m; j += nt) {
-            const int site = P.sel_idx[j];
+            const int site = j == tid && mine >= 0 ? mine : P.sel_idx[j];
             if (site < 0 || site >= nsites) { atomicOr(P.err, ERR_REPLAY); continue; }
             const int x = site % P.nx, y = site / P.nx;
             if (is_solid(P, x, y)) { atomicOr(P.err, ERR_REPLAY); continue; }
@@ -785,7 +792,8 @@ __device__ __forceinline__ void finish_parts(const Params& P, const unsigned* pe
     }
     __syncthreads();
     if (is_last) {
-        const int ng = (int)__ldcg(P.pend_count);
+        // (a kernel without pending lists, pend null, never appends to the global one)
+        const int ng = pend ? (int)__ldcg(P.pend_count) : 0;
         if (ng > 0) {
             resolve_list<L, S, EQ>(P, ng, [&](int j) { return __ldcg(P.pend_idx + j); }, &bc, &ss.sc);
             block_finish(P, bc, ss.sc);
