@@ -1659,18 +1659,22 @@ __global__ void __launch_bounds__(32 * R, tma_min_blocks<S, R, TX>())
     const int edge_items = ((P.nx > 1 ? 2 : 1) * P.ny + 32 * R - 1) / (32 * R);
     const int claims = edge_items + tiles;
 
-    // Work is handed out by a global counter: claim c < edge_items is edge
-    // item c, the others tile tile_order[c - edge_items] (boundary tiles
-    // spread over the first claims) or c - edge_items.  Thread 0 refills a
+    // Work is handed out by claims: claim c < edge_items is edge item c, the
+    // others tile tile_order[c - edge_items] (boundary tiles spread over the
+    // first claims) or c - edge_items.  Thread 0 refills a
     // stage with the work it claimed at the previous refill and claims the
     // next (the latencies of the atomic and of the order entry then overlap
     // a tile's computation), and publishes it with the stage's mbarrier:
     // the tile's index, -2 - e for edge item e, -1 when none is left (the
     // phase is then completed by a plain arrive, without a copy, as for an
     // edge item).
-    int next_claim = 0, next_tile = 0;
+    // A block's first STAGES claims are fixed (b, b + G, b + 2 G, ... for
+    // block b of G): the pipeline fills without waiting for the atomic; the
+    // counter hands out the claims from STAGES G on.
+    int next_claim = 0, next_tile = 0, fixed = 0;
     auto claim = [&]() {
-        next_claim = (int)atomicAdd(P.tile_counter, 1u);
+        if (fixed < STAGES) next_claim = (int)blockIdx.x + fixed++ * (int)gridDim.x;
+        else next_claim = (int)atomicAdd(P.tile_counter, 1u) + STAGES * (int)gridDim.x;
         const int c = next_claim - edge_items;
         next_tile = c < 0 ? -2 - next_claim : c;
         if (P.tile_order && c >= 0 && c < tiles) next_tile = __ldg(P.tile_order + c);
