@@ -414,11 +414,12 @@ const char* lb_last_error(void);
  * Many independent D2Q9 runs (each one the method of Sec. 3.2 on its own
  * grid) advanced together and replayed as CUDA graphs of 32 steps, by one of
  * three launch strategies (variants):
- *   0, 1  the batched kernel: one launch per time step covers the block
- *         tiles of every run (a flat tile list taken by a persistent grid;
- *         8-row tiles with 2 stages, or 4-row tiles with 3 stages), and the
- *         block that finishes a run's last tile performs that run's
- *         selection and Ehrenfests' step;
+ *   0, 1  the batched kernel: per time step, one stream-collide launch
+ *         covers the work of every run (a flat list of each run's edge
+ *         columns and block tiles, taken by a persistent grid; 8-row tiles
+ *         with 2 stages, or 4-row tiles with 3 stages), then one launch
+ *         performs every run's selection and Ehrenfests' step (a block per
+ *         run);
  *   2     every run's own stream-collide kernel, each run a chain of steps
  *         in its own concurrent branch of the graph.
  * Results are bit-identical to stepping each run alone with lb_step.  The paper runs

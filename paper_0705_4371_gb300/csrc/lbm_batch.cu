@@ -1,8 +1,9 @@
 // lbm_batch.cu -- batched form: many independent D2Q9 runs advanced
 // together, replayed as CUDA graphs, with an autotuner over the launch
 // strategies whose choices are cached in a JSON file.  Strategies: the
-// batched kernel (one launch per step over the tiles of every run,
-// lbm_batch_kernels.cuh) with two tile shapes, or every run's own
+// batched kernel (per step, one stream-collide launch over the work items of
+// every run and one launch of every run's selection, lbm_batch_kernels.cuh)
+// with two tile shapes, or every run's own
 // stream-collide kernel in concurrent graph branches (one chain of steps per
 // run).  All compute identical results.
 #include <algorithm>
@@ -63,7 +64,7 @@ struct lb_batch {
     Params* d_params = nullptr;          // [2][nruns]: source buffer 0, 1
     CUtensorMap* d_tmaps = nullptr;      // [2][nruns]
     int* d_tile_base = nullptr;          // [nruns + 1]
-    unsigned* d_counters = nullptr;      // [2][2 + nruns]: tile counter, runs done, tiles done
+    unsigned* d_counters = nullptr;      // [2]: the item counter of each buffer parity
     Params* h_params = nullptr;          // pinned staging of d_params
     std::vector<Params> uploaded;        // what d_params holds
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -120,7 +121,7 @@ int configure(lb_batch* b) {
         }
     CK(cudaMemcpyAsync(b->d_tmaps, tm.data(), tm.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice,
                        b->stream));
-    CK(cudaMemsetAsync(b->d_counters, 0, 2 * (2 + (size_t)n) * sizeof(unsigned), b->stream));
+    CK(cudaMemsetAsync(b->d_counters, 0, 2 * sizeof(unsigned), b->stream));
     CK(cudaStreamSynchronize(b->stream));
     return LB_OK;
 }
@@ -153,14 +154,7 @@ BatchArgs args_of(const lb_batch* b, int c) {
     A.tile_base = b->d_tile_base;
     A.nruns = n;
     A.total_tiles = b->total_tiles;
-    unsigned* cur = b->d_counters + (size_t)c * (2 + n);
-    unsigned* nxt = b->d_counters + (size_t)(1 - c) * (2 + n);
-    A.tile_counter = cur;
-    A.runs_done = cur + 1;
-    A.tiles_done = cur + 2;
-    A.next_tile_counter = nxt;
-    A.next_runs_done = nxt + 1;
-    A.next_tiles_done = nxt + 2;
+    A.tile_counter = b->d_counters + c;
     return A;
 }
 
@@ -381,7 +375,7 @@ int lb_batch_create(const lb_run_desc* runs, int n, void* cuda_stream, lb_batch*
     if (cudaMalloc(&b->d_params, 2 * (size_t)n * sizeof(Params)) != cudaSuccess ||
         cudaMalloc(&b->d_tmaps, 2 * (size_t)n * sizeof(CUtensorMap)) != cudaSuccess ||
         cudaMalloc(&b->d_tile_base, (n + 1) * sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&b->d_counters, 2 * (2 + (size_t)n) * sizeof(unsigned)) != cudaSuccess ||
+        cudaMalloc(&b->d_counters, 2 * sizeof(unsigned)) != cudaSuccess ||
         cudaMallocHost(&b->h_params, 2 * (size_t)n * sizeof(Params)) != cudaSuccess)
         return bail(fail(LB_ERR_OOM, "batch allocation failed"));
     const int rc = configure(b);

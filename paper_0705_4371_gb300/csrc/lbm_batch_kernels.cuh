@@ -1,17 +1,17 @@
 // lbm_batch_kernels.cuh -- the batched form: one launch advances every run
 // of a batch by one time step.
 //
-// The runs' block tiles (R rows x 128 sites, staged in shared memory by
-// bulk tensor copies exactly as in the single-run staged kernel: each plane's
-// window is the R rows the tile pulls from it) form one
-// flat list; a persistent grid takes tiles from a global counter, so small
-// and large runs share the GPU without idle tails per run.  A tile's sites
-// go through the same per-site update as a single run (tma_tile), its
-// pending sites are resolved before the tile is counted as done, and the
-// block that finishes a run's last tile runs that run's selection and
-// Ehrenfests' step (Sec. 3.2) while the other blocks go on with other runs'
-// tiles.  The counters of a step are selected by its buffer parity; the
-// last run to finish resets those of the next step.
+// The runs' work items (their x = 0 and x = nx - 1 columns, then their block
+// tiles of R rows x 128 sites, staged in shared memory by bulk tensor copies
+// exactly as in the single-run staged kernel: each plane's window is the R
+// rows the tile pulls from it) form one flat list; a persistent grid takes
+// items from a global counter, so small and large runs share the GPU without
+// idle tails per run.  A tile's sites go through the same per-site update
+// as a single run (tma_tile); the sites the dS bound does not clear are
+// resolved in place, and the candidates go straight to their run's global
+// list.  One block barrier per item.  A second launch (k_batch_select, one
+// block per run) then runs every run's selection and Ehrenfests' step
+// (Sec. 3.2) and resets the step's item counter.
 #pragma once
 
 #include "lbm_internal.h"
@@ -22,26 +22,11 @@ namespace lbm {
 constexpr int kBatchStage = 512;   // candidates a select stages in shared memory
 constexpr int kBatchSmemRuns = 256;   // tile bases kept in shared memory (more runs: global)
 
-// Release (or acquire-release) add at device scope: publishes the block's
-// writes, which a barrier made the calling thread observe, with the count.
-__device__ __forceinline__ unsigned atomic_add_release(unsigned* p, unsigned v) {
-    unsigned old;
-    asm volatile("atom.release.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-    return old;
-}
-
 struct BatchShared {
-    SelectShared ss;
-    // pending sites of the tile being computed; between tiles, the
-    // candidate staging of a run's selection (keys, then indices)
-    alignas(16) unsigned pend[kPend];
-    unsigned npend;
     int abort;
-    int tile[4], run[4];   // per stage: tile index within its run (-1: none left), run
-    int base[kBatchSmemRuns + 1];   // first tile of each run (batches of up to kBatchSmemRuns runs)
+    int tile[4];   // per stage: item of its run (-1: none left; -2 - e: edge item e)
+    int base[kBatchSmemRuns + 1];   // first item of each run (batches of up to kBatchSmemRuns runs)
 };
-static_assert(kBatchStage * (sizeof(unsigned long long) + sizeof(unsigned)) <= sizeof(unsigned) * kPend,
-              "candidate staging must fit in the pending list");
 static_assert(sizeof(Params) % 8 == 0, "Params is copied in 8-byte words");
 
 template <typename S, int R, int STAGES>
@@ -70,7 +55,6 @@ __global__ void __launch_bounds__(32 * R, 16 / R) k_collide_batch(const __grid_c
     if (threadIdx.x == 0) {
         for (int st = 0; st < STAGES; st++) mbar_init(&full[st], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        sh.npend = 0;
         sh.abort = 0;
     }
     const bool base_in_smem = A.nruns <= kBatchSmemRuns;
@@ -106,7 +90,6 @@ __global__ void __launch_bounds__(32 * R, 16 / R) k_collide_batch(const __grid_c
         const int nx = sp[st].nx, ny = sp[st].ny;
         const int edge_items = ((nx > 1 ? 2 : 1) * ny + 32 * R - 1) / (32 * R);
         int lt = tile - tile_base[lo];
-        sh.run[st] = lo;
         if (lt < edge_items) {
             sh.tile[st] = -2 - lt;
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -128,6 +111,8 @@ __global__ void __launch_bounds__(32 * R, 16 / R) k_collide_batch(const __grid_c
     for (;; jj++) {
         const int st = jj % STAGES;
         const unsigned parity = (unsigned)((jj / STAGES) & 1);
+        // the barrier also ends every warp's reads of the stage and the
+        // parameter slot that thread 0 refills next
         if (__syncthreads_or(!mbar_wait(&full[st], parity))) {
             if (threadIdx.x == 0) {
                 for (int q = 0; q < A.nruns; q++) atomicOr(A.P[q].err, ERR_TIMEOUT);
@@ -137,7 +122,6 @@ __global__ void __launch_bounds__(32 * R, 16 / R) k_collide_batch(const __grid_c
         }
         const int lt = sh.tile[st];
         if (lt == -1) break;
-        const int r = sh.run[st];
         if (threadIdx.x == 0) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             fill((jj + STAGES - 1) % STAGES);
@@ -149,44 +133,10 @@ __global__ void __launch_bounds__(32 * R, 16 / R) k_collide_batch(const __grid_c
         bool nonfinite = false;
         NewtonCount nc = {0, 0, 0, 0};
         const S* box = stages + (size_t)st * (LY::STAGE_BYTES / sizeof(S));
-        PendSink sink{sh.pend, &sh.npend, kPend};
+        GlobalCandSink sink;
         if (lt <= -2) edge_item<S, EQ, R>(P, -2 - lt, t, sink, mslot, nonfinite, nc);
         else tma_tile<S, EQ, R, kTmaTX, true>(P, box, tx * TX, ty * R, t, sink, mslot, nonfinite, nc, P);
-        const int nf = __syncthreads_or(nonfinite);
-        // the tile's pending sites (npend is read between barriers: uniform)
-        if (sh.npend > 0) {
-            resolve_list<L, S, EQ>(P, (int)min(sh.npend, (unsigned)kPend), [&](int j) { return sh.pend[j]; },
-                                   static_cast<BlockCand*>(nullptr), nullptr);
-            __syncthreads();
-            if (threadIdx.x == 0) sh.npend = 0;
-        }
-        // the barrier above made the tile's writes visible to thread 0; its
-        // release add publishes them with the count.  The run's last tile
-        // acquires every other tile's writes before the selection.
-        int sel = 0;
-        if (threadIdx.x == 0) {
-            if (nf) atomicOr(P.err, ERR_NONFINITE);
-            const unsigned done = atomic_add_release(A.tiles_done + r, 1u) + 1u;
-            sel = done == (unsigned)(tile_base[r + 1] - tile_base[r]);
-            if (sel) __threadfence();
-        }
-        if (__syncthreads_or(sel)) {
-            // every tile of run r is done: its selection and Ehrenfests' step
-            unsigned long long* skey = reinterpret_cast<unsigned long long*>(sh.pend);
-            unsigned* sidx = sh.pend + 2 * kBatchStage;
-            select_and_fix<L, S, EQ>(P, sh.ss, skey, sidx, kBatchStage, 0);
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                __threadfence();
-                const unsigned rd = atomicAdd(A.runs_done, 1u) + 1u;
-                if (rd == (unsigned)A.nruns) {
-                    *A.next_tile_counter = 0u;
-                    *A.next_runs_done = 0u;
-                    for (int q = 0; q < A.nruns; q++) A.next_tiles_done[q] = 0u;
-                    __threadfence();
-                }
-            }
-        }
+        if (nonfinite) atomicOr(P.err, ERR_NONFINITE);
     }
     __syncthreads();
     if (sh.abort && threadIdx.x == 0) {
@@ -198,9 +148,29 @@ __global__ void __launch_bounds__(32 * R, 16 / R) k_collide_batch(const __grid_c
     }
 }
 
+// Every run's selection and Ehrenfests' step after the batched stream-collide
+// launch (block r: run r; the parameters staged in shared memory); block 0
+// resets the step's item counter.
+template <typename S, int EQ>
+__global__ void __launch_bounds__(256) k_batch_select(const __grid_constant__ BatchArgs A) {
+    __shared__ SelectShared ss;
+    __shared__ unsigned long long skey[kBatchStage];
+    __shared__ unsigned sidx[kBatchStage];
+    __shared__ __align__(16) Params ps;
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(A.P + blockIdx.x);
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(&ps);
+    for (int k = threadIdx.x; k < (int)(sizeof(Params) / 8); k += blockDim.x) dst[k] = src[k];
+    __syncthreads();
+    select_and_fix<D2Q9, S, EQ>(ps, ss, skey, sidx, kBatchStage, 0);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *A.tile_counter = 0u;
+}
+
 template <typename S, int EQ, int R, int STAGES>
 cudaError_t launch_batch(const BatchArgs& A, int grid, cudaStream_t st) {
     k_collide_batch<S, EQ, R, STAGES><<<grid, 32 * R, batch_smem_bytes<S, R, STAGES>(), st>>>(A);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_batch_select<S, EQ><<<A.nruns, 256, 0, st>>>(A);
     return cudaGetLastError();
 }
 

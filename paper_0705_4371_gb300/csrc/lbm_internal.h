@@ -64,14 +64,9 @@ cudaError_t launch_emit_from_ds(const Params& P, const double* ds, int n, cudaSt
 struct BatchArgs {
     const Params* P;               // [nruns] the runs' parameters for this step
     const CUtensorMap* tm;         // [nruns] tensor maps of the source buffers (64-byte aligned)
-    const int* tile_base;          // [nruns + 1] first tile of each run in the flat tile list
-    int nruns, total_tiles;
-    unsigned* tile_counter;        // this step's tile counter
-    unsigned* tiles_done;          // [nruns] this step's finished tiles per run
-    unsigned* runs_done;           // this step's finished runs
-    unsigned* next_tile_counter;   // the next step's counters, reset by the last run to finish
-    unsigned* next_tiles_done;
-    unsigned* next_runs_done;
+    const int* tile_base;          // [nruns + 1] first work item of each run in the flat list
+    int nruns, total_tiles;        // total_tiles: work items (edge items and tiles) of all runs
+    unsigned* tile_counter;        // this step's item counter (reset by the step's select launch)
 };
 
 struct BatchLaunchers {

@@ -1272,6 +1272,15 @@ struct CandSink {
         count += block_push<T>(P, *bc, ds > Par<T>::delta(P), ds, site);
     }
 };
+// Resolving, with the candidates appended straight to the run's global list
+// (a kernel whose tiles belong to different runs).
+struct GlobalCandSink {
+    static constexpr bool kResolve = true;
+    template <typename T>
+    __device__ __forceinline__ void put(const Params& P, bool, T ds, unsigned site) {
+        warp_push<T>(P, ds > Par<T>::delta(P), ds, site);
+    }
+};
 
 // Pre-collision deviations of site (x, y) of a staged tile: the same rules
 // as gather_site (free flight, Sec. 4.2 boundaries).  Plane j's window holds
@@ -1471,17 +1480,16 @@ __device__ __noinline__ void edge_item(const Params& P, int item, long long t, S
 // Exact dS of the pending sites of a clean staged row (warp w: row y; lane
 // l: bit 2 s + h of pmask for column x0 + 2 l + 64 s + h), from the staged
 // planes (the same values the update read) and f* recomputed as the update
-// computed it; the candidates go to bc.  Every lane of the warp calls.
-// Returns what the warp appended.
-template <typename S, int EQ, int R, int TX, int CAP>
-__device__ __noinline__ unsigned resolve_staged_row(const Params& P, const S* box, int x0, int y, unsigned pmask,
-                                                    BlockCandT<CAP>& bc) {
+// computed it; the sites go to the sink (which keeps the candidates).  Every
+// lane of the warp calls.
+template <typename S, int EQ, int R, int TX, typename Sink>
+__device__ __noinline__ void resolve_staged_row(const Params& P, const S* box, int x0, int y, unsigned pmask,
+                                                Sink& sink) {
     using L = D2Q9;
     using T = typename Store<S>::T;
     using LY = TmaLayout<S, R, TX>;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const S* sb = box + warp * LY::W + LY::H;
-    unsigned added = 0u;
 #pragma unroll 1
     for (int b = 0; b < TX / 32; b++) {
         const int c = 2 * lane + 64 * (b >> 1) + (b & 1);
@@ -1493,9 +1501,8 @@ __device__ __noinline__ unsigned resolve_staged_row(const Params& P, const S* bo
             site_equilibrium<L, T, EQ>(P, g, gs, rho, ux, uy);
             if (!ghost_column(P, x0 + c)) ds = site_ds<L, T, EQ>(P, g, gs);
         }
-        added += block_push<T>(P, bc, ds > Par<T>::delta(P), ds, (unsigned)(y * P.nx + x0 + c));
+        sink.put(P, false, ds, (unsigned)(y * P.nx + x0 + c));
     }
-    return added;
 }
 
 // One staged tile: rows y0 .. y0 + R - 1 and columns x0 .. x0 + 127 of the
@@ -1602,8 +1609,7 @@ __device__ __forceinline__ void tma_tile(const Params& P, const S* box, int x0, 
         if constexpr (Sink::kResolve) {
             // the row's pending sites, from the staged planes (valid until the
             // next tile's barrier), out of line: the update keeps its registers
-            if (__any_sync(0xffffffffu, pmask != 0u))
-                sink.count += resolve_staged_row<S, EQ, R, TX>(Pc, box, x0, y, pmask, *sink.bc);
+            if (__any_sync(0xffffffffu, pmask != 0u)) resolve_staged_row<S, EQ, R, TX>(Pc, box, x0, y, pmask, sink);
         }
         return;
     }
