@@ -1156,11 +1156,12 @@ __global__ void __launch_bounds__(32 * WARPS, MINB) k_collide_d2q9(const __grid_
 // x0 + 128 + H (H elements = 16 bytes on each side, which keeps every copy
 // 16-byte aligned).  Copies complete on an mbarrier; STAGES tiles are in
 // flight per block, so the bytes in flight do not depend on registers.
-// Warp w computes row w of the tile, lane l the sites x0 + l + 32 s
-// (s = 0..3): shared-memory reads and global stores are both consecutive
-// across the warp.  In tiles that touch a boundary or the obstacle the sites
-// use the rule-by-rule gather, from shared memory where the source lies in
-// its plane's window and from the source field otherwise.  Every wait on an
+// Warp w computes row w of the tile, lane l the site pairs x0 + 2 l + 64 s,
+// + 1: shared-memory reads and global stores are both consecutive across the
+// warp.  In tiles that touch the y sides or the obstacle the sites use the
+// rule-by-rule gather, from shared memory where the source lies in its
+// plane's window and from the source field otherwise; the x = 0 and
+// x = nx - 1 columns are edge items of their own.  Every wait on an
 // mbarrier is bounded: on expiry the block flags ERR_TIMEOUT, stops issuing
 // copies, waits (bounded) for the copies it issued, and ends.
 // ---------------------------------------------------------------------------
@@ -1245,39 +1246,25 @@ constexpr size_t tma_smem_bytes() {
            (EQ == EQ_ENERGY_MLP ? sizeof(MlpSlot<EQ>) + 16 : 0);
 }
 
-// Where a staged tile's updated sites go (put: every lane of the warp calls,
-// with its site's pending flag and, for a sink that resolves, its dS).
-// PendSink: the sites the dS bound does not clear, to a pending list whose
-// exact dS is evaluated later from the source field.  CandSink: the dS of
-// those sites is evaluated in the update itself (update_site, RESOLVE) and
-// the candidates (dS > delta) go to the block's buffer; count is what the
-// warp appended since the block's last cut (the same on every lane).
-struct PendSink {
-    static constexpr bool kResolve = false;
-    unsigned* list;
-    unsigned* n;
-    int cap;
-    template <typename T>
-    __device__ __forceinline__ void put(const Params& P, bool pending, T, unsigned site) {
-        warp_pend(P, list, n, cap, pending, site);
-    }
-};
+// Where a staged tile's candidates go (put: every lane of the warp calls,
+// with its site's dS, -1 for a site the dS bound cleared; the sites the
+// bound does not clear have their exact dS evaluated on the tile, from the
+// staged planes or in the update).  CandSink: the block's buffer; count is
+// what the warp appended since the block's last cut (the same on every
+// lane).  GlobalCandSink: the run's global list (a kernel whose tiles belong
+// to different runs).
 template <int CAP>
 struct CandSink {
-    static constexpr bool kResolve = true;
     BlockCandT<CAP>* bc;
     unsigned count;
     template <typename T>
-    __device__ __forceinline__ void put(const Params& P, bool, T ds, unsigned site) {
+    __device__ __forceinline__ void put(const Params& P, T ds, unsigned site) {
         count += block_push<T>(P, *bc, ds > Par<T>::delta(P), ds, site);
     }
 };
-// Resolving, with the candidates appended straight to the run's global list
-// (a kernel whose tiles belong to different runs).
 struct GlobalCandSink {
-    static constexpr bool kResolve = true;
     template <typename T>
-    __device__ __forceinline__ void put(const Params& P, bool, T ds, unsigned site) {
+    __device__ __forceinline__ void put(const Params& P, T ds, unsigned site) {
         warp_push<T>(P, ds > Par<T>::delta(P), ds, site);
     }
 };
@@ -1374,7 +1361,6 @@ __device__ __noinline__ void tma_tile_general(const Params& P, const S* box, int
 #pragma unroll 1
     for (int s = 0; s < TX / 32; s++) {
         const int x = x0 + lane + 32 * s;
-        bool pend = false;
         T ds = T(-1);
         // the learned form enters with every lane (its warm start is a
         // warp-wide evaluation); lanes outside the grid then carry no site
@@ -1408,18 +1394,16 @@ __device__ __noinline__ void tma_tile_general(const Params& P, const S* box, int
             } else {
                 gather_site_smem<S, R, TX>(P, box, x0, y0, x, y, g);
             }
-            constexpr bool kR = Sink::kResolve;
             if constexpr (EQ == EQ_ENERGY_MLP) {
                 float a0[3];
                 __syncwarp();
                 mlp_site_start<T>(P, mslot.s, fluid, g, a0);
                 if (fluid)
-                    pend = update_site<L, T, EQ, Store<S>::kProject, true, kR>(P, g, x, y, t, nonfinite, nc, a0,
-                                                                               &ds);
+                    update_site<L, T, EQ, Store<S>::kProject, true, true>(P, g, x, y, t, nonfinite, nc, a0, &ds);
             } else {
                 if (fluid)
-                    pend = update_site<L, T, EQ, Store<S>::kProject, true, kR>(P, g, x, y, t, nonfinite, nc,
-                                                                               nullptr, &ds);
+                    update_site<L, T, EQ, Store<S>::kProject, true, true>(P, g, x, y, t, nonfinite, nc, nullptr,
+                                                                          &ds);
             }
             if (inside) {
 #pragma unroll
@@ -1427,7 +1411,7 @@ __device__ __noinline__ void tma_tile_general(const Params& P, const S* box, int
                     Store<S>::store(dst + i * plane + o, 0, fluid ? store_round<L, S>(i, g[i]) : g[i]);
             }
         }
-        sink.put(P, pend, ds, (unsigned)(y * P.nx + x));
+        sink.put(P, ds, (unsigned)(y * P.nx + x));
     }
 }
 
@@ -1456,16 +1440,14 @@ __device__ __noinline__ void edge_item(const Params& P, int item, long long t, S
 #pragma unroll
         for (int i = 0; i < L::Q; i++) g[i] = T(0);
     }
-    bool pend = false;
     T ds = T(-1);
-    constexpr bool kR = Sink::kResolve;
     if constexpr (EQ == EQ_ENERGY_MLP) {
         float a0[3];
         mlp_site_start<T>(P, mslot.s, fluid, g, a0);
-        if (fluid) pend = update_site<L, T, EQ, Store<S>::kProject, true, kR>(P, g, x, y, t, nonfinite, nc, a0, &ds);
+        if (fluid) update_site<L, T, EQ, Store<S>::kProject, true, true>(P, g, x, y, t, nonfinite, nc, a0, &ds);
     } else {
         if (fluid)
-            pend = update_site<L, T, EQ, Store<S>::kProject, true, kR>(P, g, x, y, t, nonfinite, nc, nullptr, &ds);
+            update_site<L, T, EQ, Store<S>::kProject, true, true>(P, g, x, y, t, nonfinite, nc, nullptr, &ds);
     }
     if (inside) {
         S* dst = static_cast<S*>(P.dst);
@@ -1474,7 +1456,7 @@ __device__ __noinline__ void edge_item(const Params& P, int item, long long t, S
         for (int i = 0; i < L::Q; i++)
             Store<S>::store(dst, i * P.plane + o, fluid ? store_round<L, S>(i, g[i]) : g[i]);
     }
-    sink.put(P, pend, ds, (unsigned)(y * P.nx + x));
+    sink.put(P, ds, (unsigned)(y * P.nx + x));
 }
 
 // Exact dS of the pending sites of a clean staged row (warp w: row y; lane
@@ -1501,7 +1483,7 @@ __device__ __noinline__ void resolve_staged_row(const Params& P, const S* box, i
             site_equilibrium<L, T, EQ>(P, g, gs, rho, ux, uy);
             if (!ghost_column(P, x0 + c)) ds = site_ds<L, T, EQ>(P, g, gs);
         }
-        sink.put(P, false, ds, (unsigned)(y * P.nx + x0 + c));
+        sink.put(P, ds, (unsigned)(y * P.nx + x0 + c));
     }
 }
 
@@ -1537,7 +1519,6 @@ __device__ __forceinline__ void tma_tile(const Params& P, const S* box, int x0, 
                             P.probe_x >= x0 && P.probe_x < x0 + TX;
     if (clean && !probe_here) {
         const int row = y * nxp + x0;
-        const unsigned site0 = (unsigned)(y * P.nx + x0);
         unsigned pmask = 0u;   // pending sites of the lane (bit 2 s + h: column 2 l + 64 s + h)
         const bool edge_tile = SPLIT && (x0 == 0 || x0 + TX >= P.nx - 1);
         // two adjacent sites per lane, columns c and c + 1 (c = 2 l + 64 s):
@@ -1599,18 +1580,11 @@ __device__ __forceinline__ void tma_tile(const Params& P, const S* box, int x0, 
             }
             pa = pa && !ea;
             pb = pb && !eb;
-            if constexpr (Sink::kResolve) {
-                pmask |= ((pa ? 1u : 0u) | (pb ? 2u : 0u)) << (2 * s);
-            } else {
-                sink.put(P, pa, T(-1), site0 + (unsigned)c);
-                sink.put(P, pb, T(-1), site0 + (unsigned)c + 1u);
-            }
+            pmask |= ((pa ? 1u : 0u) | (pb ? 2u : 0u)) << (2 * s);
         }
-        if constexpr (Sink::kResolve) {
-            // the row's pending sites, from the staged planes (valid until the
-            // next tile's barrier), out of line: the update keeps its registers
-            if (__any_sync(0xffffffffu, pmask != 0u)) resolve_staged_row<S, EQ, R, TX>(Pc, box, x0, y, pmask, sink);
-        }
+        // the row's pending sites, from the staged planes (valid until the
+        // next tile's barrier), out of line: the update keeps its registers
+        if (__any_sync(0xffffffffu, pmask != 0u)) resolve_staged_row<S, EQ, R, TX>(Pc, box, x0, y, pmask, sink);
         return;
     }
     tma_tile_general<S, EQ, R, TX, SPLIT>(Pc, box, x0, y0, t, sink, mslot, nonfinite, nc, clean);
