@@ -266,6 +266,7 @@ def run_gpu(args):
                 "avg_launch_ms": round(coll_ms, 5),
                 "avg_launch_ms_source": "timed region / launches (one launch per step, gaps included)",
                 "event_bracketed_launch_ms": round(bracketed_ms, 5) if bracketed_ms else None,
+                "step_frac_of_peak": round(alg_bytes * args.steps / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
                 "peak_source": peaks["source"] + " hbm_gbs",
                 "frac_of_nominal_8TBps": round(achieved / 8000.0, 4)}
 
