@@ -64,17 +64,21 @@ __global__ void __launch_bounds__(32 * R, 16 / R) k_collide_batch(const __grid_c
     const int* tile_base = base_in_smem ? sh.base : A.tile_base;
     int run_hint = 0;   // tiles are claimed in increasing order: runs only move forward
 
-    // Thread 0 claims the next tile, copies its run's parameters into the
-    // stage's slot and issues the copies; the stage's mbarrier publishes
-    // both (-1: no tile left; the phase then completes by a plain arrive).
+    // Thread 0 takes the item it claimed at the previous refill and claims
+    // the next (the atomic's latency then overlaps an item's computation),
+    // copies the item's run parameters into the stage's slot and issues the
+    // copies; the stage's mbarrier publishes both (-1: no item left; the
+    // phase then completes by a plain arrive).
+    int next_item = 0;   // claimed at the previous refill (the atomic's latency overlaps an item)
     auto fill = [&](int st) {
         unsigned long long* bar = &full[st];
-        const int tile = (int)atomicAdd(A.tile_counter, 1u);
+        const int tile = next_item;
         if (tile >= A.total_tiles) {
             sh.tile[st] = -1;
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
             return;
         }
+        next_item = (int)atomicAdd(A.tile_counter, 1u);
         int lo = run_hint;   // the last run whose first tile is <= tile
         while (tile_base[lo + 1] <= tile) lo++;
         run_hint = lo;
@@ -105,8 +109,10 @@ __global__ void __launch_bounds__(32 * R, 16 / R) k_collide_batch(const __grid_c
         for (int i = 0; i < L::Q; i++)
             tma_load_3d(base + i * LY::PLANE, A.tm + lo, tx * TX - LY::H, ty * R - L::cy(i), i, bar);
     };
-    if (threadIdx.x == 0)
+    if (threadIdx.x == 0) {
+        next_item = (int)atomicAdd(A.tile_counter, 1u);
         for (int st = 0; st < STAGES - 1; st++) fill(st);
+    }
     int jj = 0;
     for (;; jj++) {
         const int st = jj % STAGES;
