@@ -26,8 +26,18 @@ struct BatchShared {
     int abort;
     int tile[4];   // per stage: item of its run (-1: none left; -2 - e: edge item e)
     int base[kBatchSmemRuns + 1];   // first item of each run (batches of up to kBatchSmemRuns runs)
+    int dims[kBatchSmemRuns][2];    // nx, ny of each run
 };
-static_assert(sizeof(Params) % 8 == 0, "Params is copied in 8-byte words");
+static_assert(sizeof(Params) % 16 == 0, "Params is copied by a bulk copy (16-byte multiples)");
+
+// Bulk copy of bytes (a multiple of 16, both addresses 16-byte aligned) from
+// global to shared memory, completing on the mbarrier's transaction count.
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(reinterpret_cast<unsigned long long>(src)), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
 
 template <typename S, int R, int STAGES>
 constexpr size_t batch_params_offset() {
@@ -59,16 +69,23 @@ __global__ void __launch_bounds__(32 * R, 16 / R) k_collide_batch(const __grid_c
     }
     const bool base_in_smem = A.nruns <= kBatchSmemRuns;
     if (base_in_smem)
-        for (int q = threadIdx.x; q <= A.nruns; q += blockDim.x) sh.base[q] = A.tile_base[q];
+        for (int q = threadIdx.x; q <= A.nruns; q += blockDim.x) {
+            sh.base[q] = A.tile_base[q];
+            if (q < A.nruns) {
+                sh.dims[q][0] = A.P[q].nx;
+                sh.dims[q][1] = A.P[q].ny;
+            }
+        }
     __syncthreads();
     const int* tile_base = base_in_smem ? sh.base : A.tile_base;
     int run_hint = 0;   // tiles are claimed in increasing order: runs only move forward
 
     // Thread 0 takes the item it claimed at the previous refill and claims
     // the next (the atomic's latency then overlaps an item's computation),
-    // copies the item's run parameters into the stage's slot and issues the
-    // copies; the stage's mbarrier publishes both (-1: no item left; the
-    // phase then completes by a plain arrive).
+    // issues a bulk copy of the item's run parameters into the stage's slot
+    // and the tile's copies, all completing on the stage's mbarrier (-1: no
+    // item left; the phase then completes by a plain arrive).  The run's nx
+    // and ny, which place the tile, come from a table in shared memory.
     int next_item = 0;   // claimed at the previous refill (the atomic's latency overlaps an item)
     auto fill = [&](int st) {
         unsigned long long* bar = &full[st];
@@ -82,28 +99,24 @@ __global__ void __launch_bounds__(32 * R, 16 / R) k_collide_batch(const __grid_c
         int lo = run_hint;   // the last run whose first tile is <= tile
         while (tile_base[lo + 1] <= tile) lo++;
         run_hint = lo;
-        const unsigned long long* src = reinterpret_cast<const unsigned long long*>(A.P + lo);
-        unsigned long long* dst = reinterpret_cast<unsigned long long*>(sp + st);
-        unsigned long long w[sizeof(Params) / 8];
-#pragma unroll
-        for (int k = 0; k < (int)(sizeof(Params) / 8); k++) w[k] = __ldg(src + k);
-#pragma unroll
-        for (int k = 0; k < (int)(sizeof(Params) / 8); k++) dst[k] = w[k];
         // a run's work: its edge items (the x = 0 and x = nx - 1 columns,
         // 32 R sites each), then its tiles
-        const int nx = sp[st].nx, ny = sp[st].ny;
+        const int nx = base_in_smem ? sh.dims[lo][0] : A.P[lo].nx;
+        const int ny = base_in_smem ? sh.dims[lo][1] : A.P[lo].ny;
         const int edge_items = ((nx > 1 ? 2 : 1) * ny + 32 * R - 1) / (32 * R);
         int lt = tile - tile_base[lo];
         if (lt < edge_items) {
             sh.tile[st] = -2 - lt;
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+            mbar_expect_tx(bar, (unsigned)sizeof(Params));
+            bulk_copy_g2s(sp + st, A.P + lo, (unsigned)sizeof(Params), bar);
             return;
         }
         lt -= edge_items;
         sh.tile[st] = lt;
         const int tiles_x = (nx + TX - 1) / TX;
         const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
-        mbar_expect_tx(bar, (unsigned)LY::TX_BYTES);
+        mbar_expect_tx(bar, (unsigned)(LY::TX_BYTES + sizeof(Params)));
+        bulk_copy_g2s(sp + st, A.P + lo, (unsigned)sizeof(Params), bar);
         S* base = stages + (size_t)st * (LY::STAGE_BYTES / sizeof(S));
 #pragma unroll
         for (int i = 0; i < L::Q; i++)

@@ -121,6 +121,7 @@ struct Params {
     // the stream-collide launch ends with the slab's own k best candidates
     // (select only), the global selection being applied afterwards
     int slab, own_x0, own_x1;
+    int pad_[2];              // size a multiple of 16 bytes (bulk copies)
 };
 
 template <int Q, typename T> struct PopArr { T v[Q]; };
