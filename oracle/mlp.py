@@ -128,6 +128,36 @@ def forward(p, feat, round=True, band=0.0):
     return y, cache
 
 
+def forward_bounds(p, feat, band):
+    """Bounds [y_lo, y_hi] of the outputs of every evaluation of the rounded
+    network whose hidden pre-activations z stray from their exact values by
+    at most band x the sum of the absolute values of z's terms (the FP32
+    accumulation of the kernels, in any order).  Rounding to BF16 and the
+    ReLU are monotone, so a hidden value lies between the roundings of the
+    ends of its z interval; hidden values are >= 0, so the next layer's
+    interval takes the positive weights at the same end and the negative
+    ones at the other.  The output layer's own accumulation error is left to
+    the caller's tolerance.  With band = 0 both bounds are forward's y (up to
+    the order of the FP64 sums)."""
+    d = unpack(p)
+    x = standardise(p, feat, True)
+    W1, W2, W3 = bf16(d["W1"]), bf16(d["W2"]), bf16(d["W3"])
+    z1 = x @ W1.T + d["b1"]
+    m1 = np.abs(x) @ np.abs(W1).T + np.abs(d["b1"])
+    h1lo = bf16(np.maximum(z1 - band * m1, 0.0))
+    h1hi = bf16(np.maximum(z1 + band * m1, 0.0))
+    W2p, W2n = np.maximum(W2, 0.0), np.minimum(W2, 0.0)
+    z2lo = h1lo @ W2p.T + h1hi @ W2n.T + d["b2"]
+    z2hi = h1hi @ W2p.T + h1lo @ W2n.T + d["b2"]
+    m2 = h1hi @ np.abs(W2).T + np.abs(d["b2"])
+    h2lo = bf16(np.maximum(z2lo - band * m2, 0.0))
+    h2hi = bf16(np.maximum(z2hi + band * m2, 0.0))
+    W3p, W3n = np.maximum(W3, 0.0), np.minimum(W3, 0.0)
+    ylo = h2lo @ W3p.T + h2hi @ W3n.T + d["b3"]
+    yhi = h2hi @ W3p.T + h2lo @ W3n.T + d["b3"]
+    return ylo, yhi
+
+
 def loss_and_grad(p, feat, dmu, round=True):
     """Mean squared error against dmu / out_scale and its gradient with
     respect to the parameters (the standardisation and output-scale entries

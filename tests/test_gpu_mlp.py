@@ -5,8 +5,8 @@ training, the learned run's trajectory, and what the network gains.
 The network's forward pass rounds hidden pre-activations accumulated in FP32
 to BF16; where the oracle's FP64 value lies within a hair of a rounding
 boundary the two sides may round differently, so the element-wise checks use
-the samples the oracle flags as unambiguous (the flagged ones are only
-counted)."""
+the samples the oracle flags as unambiguous, and every sample, the flagged
+ones included, is held inside the oracle's bounds over all such roundings."""
 import numpy as np
 import pytest
 
@@ -88,9 +88,17 @@ def test_forward_matches_oracle(env):
     mag = c["h2"] @ np.abs(omlp.bf16(d["W3"])).T + np.abs(d["b3"])
     ok = ~amb
     err = np.abs(yg - yo)[ok] / mag[ok]
-    print("forward: %d of %d samples ambiguous; max error / magnitude %.3g" % (amb.sum(), n, err.max()))
+    # every sample, the ambiguous ones included: inside the bounds of all
+    # evaluations whose hidden sums stray by at most the band
+    lo, hi = omlp.forward_bounds(p, feat, BAND)
+    out = np.maximum(lo - yg, yg - hi) / mag
+    width = (hi - lo) / mag
+    print("forward: %d of %d samples ambiguous; max error / magnitude %.3g; all samples: "
+          "worst excess over the bounds %.3g (interval width max %.3g, %d samples wider than 1e-5)"
+          % (amb.sum(), n, err.max(), out.max(), width.max(), int(np.sum(width.max(1) > 1e-5))))
     assert amb.mean() < 0.3
     assert err.max() <= 1e-5
+    assert out.max() <= 1e-5
 
 
 def _clean_batch(p, seed, n):

@@ -120,3 +120,107 @@ def test_near_boundary_flags():
     mag = np.ones_like(z)
     f = mlp._near_boundary(z, mag, 1e-5)
     assert f.tolist() == [[True, False, True, False]]
+
+
+def _fp32_accumulated_forward(p, feat, seed):
+    """The rounded network evaluated as a kernel would: products of BF16
+    values (exact in FP32) and the FP32 bias summed in FP32 in a random order
+    per unit, hidden values rounded to BF16 after the ReLU.  Also returns the
+    largest error of a hidden pre-activation sum relative to the sum of the
+    absolute values of its terms."""
+    d = mlp.unpack(p)
+    g = np.random.default_rng(seed)
+    f32 = np.float32
+    x = mlp.standardise(p, feat, True).astype(f32)
+    worst = [0.0]
+
+    def layer(h, W, b, hidden=True):
+        terms = np.concatenate([h[:, None, :] * mlp.bf16(W).astype(f32)[None, :, :],
+                                np.broadcast_to(b.astype(f32), (h.shape[0], b.size))[:, :, None]], axis=2)
+        order = np.argsort(g.random(terms.shape), axis=2)
+        terms = np.take_along_axis(terms, order, axis=2).astype(f32)
+        s = np.zeros(terms.shape[:2], f32)
+        for k in range(terms.shape[2]):
+            s = (s + terms[:, :, k]).astype(f32)
+        if hidden:
+            t64 = terms.astype(np.float64)
+            worst[0] = max(worst[0], float(np.max(np.abs(s - t64.sum(2)) / np.abs(t64).sum(2))))
+        return s
+
+    h1 = mlp.bf16(np.maximum(layer(x, d["W1"], d["b1"]), 0)).astype(f32)
+    h2 = mlp.bf16(np.maximum(layer(h1, d["W2"], d["b2"]), 0)).astype(f32)
+    return layer(h2, d["W3"], d["b3"], hidden=False).astype(np.float64), worst[0]
+
+
+@pytest.mark.parametrize("band", [4e-6, 2.5e-7])
+def test_forward_bounds_hold_every_fp32_accumulation_order(band):
+    # Every order of the hidden sums whose error stays within band x the sum
+    # of |terms| must give outputs inside the bounds (up to the output sum's
+    # own FP32 error).  4e-6 covers the worst case of an FP32 sum of 65
+    # terms (65 u / (1 - 65 u), u = 2^-24); 2.5e-7, the band of the GPU
+    # check, covers the errors these orders make (asserted), and gives
+    # bounds tight enough that a missing widening at either layer shows.
+    p = random_params(51)
+    feat = random_features(52, 1024)
+    lo, hi = mlp.forward_bounds(p, feat, band)
+    y, c = mlp.forward(p, feat, round=True)
+    d = mlp.unpack(p)
+    mag = c["h2"] @ np.abs(mlp.bf16(d["W3"])).T + np.abs(d["b3"])
+    tol = 4e-6 * mag
+    assert np.all(lo <= y + 1e-12 * mag) and np.all(y <= hi + 1e-12 * mag)
+    moved = 0
+    for seed in range(12):
+        ys, worst = _fp32_accumulated_forward(p, feat, 600 + seed)
+        assert worst <= band, (seed, worst)
+        assert np.all(ys >= lo - tol) and np.all(ys <= hi + tol), seed
+        moved += int(np.sum(np.abs(ys - y) > tol))
+    # some orders flip a hidden rounding (the bounds are exercised, not trivial)
+    assert moved > 0
+    assert np.any(hi - lo > 10 * tol)
+
+
+def test_forward_bounds_contain_every_perturbed_evaluation():
+    # The bounds' definition by brute force: every hidden pre-activation
+    # moved anywhere within band x the sum of its |terms| (uniformly inside,
+    # and at both ends of the interval), the network evaluated in FP64 from
+    # there; each output must lie inside the bounds.
+    p = random_params(55)
+    feat = random_features(56, 2048)
+    band = 2.5e-7
+    lo, hi = mlp.forward_bounds(p, feat, band)
+    d = mlp.unpack(p)
+    x = mlp.standardise(p, feat, True)
+    W1, W2, W3 = mlp.bf16(d["W1"]), mlp.bf16(d["W2"]), mlp.bf16(d["W3"])
+    g = np.random.default_rng(57)
+
+    def shift(shape):
+        u = g.uniform(-1.0, 1.0, shape)
+        pick = g.random(shape)
+        u[pick < 0.25] = -(1 - 1e-9)
+        u[pick > 0.75] = 1 - 1e-9
+        return u
+
+    ymin, ymax = np.full(lo.shape, np.inf), np.full(lo.shape, -np.inf)
+    outside = 0
+    for _ in range(16):
+        z1 = x @ W1.T + d["b1"]
+        z1 = z1 + band * (np.abs(x) @ np.abs(W1).T + np.abs(d["b1"])) * shift(z1.shape)
+        h1 = mlp.bf16(np.maximum(z1, 0.0))
+        z2 = h1 @ W2.T + d["b2"]
+        z2 = z2 + band * (h1 @ np.abs(W2).T + np.abs(d["b2"])) * shift(z2.shape)
+        h2 = mlp.bf16(np.maximum(z2, 0.0))
+        y = h2 @ W3.T + d["b3"]
+        mag = h2 @ np.abs(W3).T + np.abs(d["b3"])
+        outside += int(np.sum((y < lo - 1e-12 * mag) | (y > hi + 1e-12 * mag)))
+        ymin, ymax = np.minimum(ymin, y), np.maximum(ymax, y)
+    assert outside == 0
+    # the perturbations reach far into the wide intervals (not point checks)
+    assert (ymax - ymin).max() > 0.25 * (hi - lo).max() > 0
+
+
+def test_forward_bounds_collapse_to_forward_without_band():
+    p = random_params(53)
+    feat = random_features(54, 256)
+    y, _ = mlp.forward(p, feat, round=True)
+    lo, hi = mlp.forward_bounds(p, feat, 0.0)
+    assert np.allclose(lo, y, rtol=0, atol=1e-12) and np.allclose(hi, y, rtol=0, atol=1e-12)
