@@ -48,6 +48,20 @@ def warm_graphs(h):
     h.sync()
 
 
+SPACER_CYCLES = 1_000_000   # about 0.5 ms of device time at 2 GHz
+
+
+def device_spacer(stream):
+    """Untimed, inside the synchronised brackets: a sleep kernel on the
+    timed stream, so that the device is still busy while the host enqueues
+    the first event and the timed launches, and the first event is stamped
+    when the device can start the first step, not while it waits for the
+    host's first submission (tens of microseconds through ctypes)."""
+    import torch
+    with torch.cuda.stream(stream):
+        torch.cuda._sleep(SPACER_CYCLES)
+
+
 def timed_steps(h, stream, n):
     """Milliseconds of n steps through the library's own path (CUDA graphs of
     programmatically dependent launches; direct launches for a remainder
@@ -56,6 +70,7 @@ def timed_steps(h, stream, n):
     h.set_timing(False)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    device_spacer(stream)
     e0.record(stream)
     h.step(n)
     e1.record(stream)
@@ -240,6 +255,7 @@ def run_gpu(args):
     with ClockSampler(local) as clocks:
         torch.cuda.synchronize()
         barrier()
+        device_spacer(stream)
         ev0.record(stream)
         g.step(args.steps)
         ev1.record(stream)
@@ -414,6 +430,7 @@ def c2_form(args, stream):
         h2.step(args.spinup)
         h2.sync()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        device_spacer(stream)
         e0.record(stream)
         h2.step(args.form_steps)
         e1.record(stream)
@@ -458,6 +475,7 @@ def learned_form(args, stream):
             h2.kernel_times(reset=True)
             h2.newton_stats(reset=True)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            device_spacer(stream)
             e0.record(stream)
             h2.step(args.learned_steps)
             e1.record(stream)
@@ -525,6 +543,7 @@ def batched_form(args, stream, peaks, world=1, rank=0):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             barrier()
+            device_spacer(stream)
             e0.record(stream)
             fn(n)
             e1.record(stream)
