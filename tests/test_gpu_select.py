@@ -55,3 +55,10 @@ def test_select_only_strict_threshold(lbm):
     ds = np.array([1e-3, 2e-3, 1e-3, 5e-4, np.inf, 0.0])
     assert list(lbm.select_only(ds, 1e-3, 10)) == [1, 4]
     assert list(lbm.select_only(ds, 1e-3, 0)) == []
+
+
+def test_select_only_empty_input(lbm):
+    ds = np.zeros(0)
+    for k in (0, 1, 16):
+        assert lbm.select_only(ds, 0.0, k).size == 0
+        assert ora.select(ds, 0.0, k).size == 0

@@ -79,3 +79,24 @@ def test_rejects_sizes_beyond_the_fixed_memory(env):
                                 cnt.data_ptr())
     assert e.value.code == lbm.LB_ERR_ARG
     assert "exceeds" in str(e.value)
+
+
+def test_empty_and_largest_inputs(env):
+    torch, lbm = env
+    # no values: the count is written (0), nothing is selected
+    assert _noalloc_select(torch, lbm, np.zeros(0), 0.0, 8).size == 0
+    # the largest n the fixed working memory holds, every value a candidate
+    n = lbm.NOALLOC_MAX_N
+    ds = inputs.random_ds_with_ties(3003, n, n_ties=2000, frac_inf=0.001)
+    for k in (1, 1000):
+        got = _noalloc_select(torch, lbm, ds, -1.0, k)
+        assert np.array_equal(got, ora.select(ds, -1.0, k))
+    # one more is refused on the host, before any launch (the buffers are
+    # real and large enough all the same)
+    dev = torch.device("cuda", 0)
+    big = torch.zeros(n + 1, dtype=torch.float64, device=dev)
+    out = torch.zeros(4, dtype=torch.int32, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+    with pytest.raises(lbm.LBError, match="fixed working memory"):
+        lbm.select_only_noalloc(big.data_ptr(), n + 1, 0.0, 4, out.data_ptr(), cnt.data_ptr())
+    torch.cuda.synchronize(dev)
