@@ -337,8 +337,11 @@ int lb_kernel_times(lb_handle* h, double* collide_ms, long long* collide_launche
  * population plane, of the R rows of the R x C-site block tile's sources in
  * that plane plus 16 bytes of halo columns; R rows, C columns, STAGES tiles
  * in flight per block): 4 = 8 x 128, STAGES 2 (default of FP64 storage);
- * 5 = 6 x 128, STAGES 3 (default of FP32 and FP16 storage, plain and
- * deviation);  6 = 8 x 64, STAGES 2 (three blocks per SM).  The
+ * 5 = 6 x 128, STAGES 3 (default of FP16 storage and of FP32 storage, plain
+ * and deviation, above 600 000 sites; FP32 storage with the polynomial
+ * quasiequilibrium up to 600 000 sites defaults to the register-fed shape
+ * 1);  6 = 8 x 64, STAGES 2 (three blocks
+ * per SM).  The
  * energy-constrained forms are built for shapes 0 (1, 8, 2: 128 registers
  * per thread), 1 (2 and 3 run 1), 4 and 5, and refuse 6 (LB_ERR_ARG); their
  * defaults: 1 for FP64 storage, 4 for FP32 / FP16 storage (Newton start and

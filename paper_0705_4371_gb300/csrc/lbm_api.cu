@@ -48,15 +48,24 @@ constexpr int kDefaultLog = 65536;
 // (plain and deviation) stage 6-row tiles with 2 more in flight per block
 // (shape 5; FP16 at 1000 steps of the 4096 x 2048 cylinder: 90.8 k MLUPS
 // against 86.8 k with 8-row tiles at three blocks per SM); FP64 storage
-// 8-row tiles with 1 more (shape 4).  The energy forms are bound by the Newton solve, not
+// 8-row tiles with 1 more (shape 4).  Small polynomial-f* FP32 grids (up to 600 000 sites:
+// one or two staged tiles per resident block, a step of ~20 us dominated by
+// latency) run faster register-fed (shape 1): the 600 x 500 channel 15.7 k
+// against 13.0 k MLUPS, 1024 x 512 23.2 k against 22.2 k; from 1536 x 768
+// on shape 5 is ahead (34.3 k against 31.1 k), and FP16 storage is fastest
+// on shape 5 at every size measured.  The energy forms are bound by the Newton solve, not
 // by memory: FP64 storage's FP64 finish wants the most resident warps
 // (register-fed shape 1); the float-float finish of FP32 / FP16 storage and
 // the network's warm start run best in the staged shape 4 (measured at
 // 2048 x 1024: Newton start 0.22 ms per step against 0.44 on shape 0 and 0.24
 // on shape 5; warm start 0.35 against 0.54 and 0.35).
-int default_tile_shape(int lattice, int eq, int precision) {
+int default_tile_shape(int lattice, int eq, int precision, long long sites) {
     if (lattice != LB_D2Q9) return 0;
-    if (eq < LB_EQ_ENTROPIC_ENERGY) return precision == LB_F64 ? 4 : 5;
+    if (eq < LB_EQ_ENTROPIC_ENERGY) {
+        if (precision == LB_F64) return 4;
+        if (eq == LB_EQ_POLY && precision != LB_F16_DEV && sites <= 600000) return 1;
+        return 5;
+    }
     if (precision == LB_F64) return 1;
     return 4;
 }
@@ -530,7 +539,7 @@ int lb_create(int lattice, int nx, int ny, int equilibrium, double nu, double de
     h->bc = b;
     h->plane = (long long)ny * h->nxp;
     h->probe_x = h->probe_y = -1;
-    h->tile_shape = default_tile_shape(lattice, equilibrium, precision);
+    h->tile_shape = default_tile_shape(lattice, equilibrium, precision, (long long)nx * ny);
     h->ring_cap = kDefaultLog;
     h->replay_t0 = -1;
     if (precision == LB_F64) h->L = launchers_f64(lattice, equilibrium);

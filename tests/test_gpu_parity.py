@@ -254,6 +254,24 @@ def test_tile_shapes_give_identical_results(lbm, shape, prec, outlet):
     assert np.array_equal(ref.counts(50), g.counts(50))
 
 
+def test_default_tile_shapes_follow_grid_size(lbm):
+    # staged 6-row tiles (shape 5) for large FP32 / FP16 grids, register-fed
+    # tiles (shape 1) for polynomial-f* FP32 grids up to 600 000 sites, 8-row
+    # staged tiles (shape 4) for FP64 storage
+    small = inputs.workload_c2(1000.0)                              # 300 000 sites
+    edge = inputs.cylinder(1000, 600, 24, 1000.0)                   # 600 000 sites
+    large = inputs.cylinder(1200, 600, 24, 1000.0)                  # 720 000 sites
+    want = [("f32", small, 1), ("f32dev", small, 1), ("f32", edge, 1), ("f32dev", large, 5),
+            ("f16dev", small, 5), ("f64", small, 4)]
+    for prec, w, shape in want:
+        g = gpu_run(lbm, w, prec)
+        assert g.info()["tile_shape"] == shape, (prec, w.nx, w.ny)
+        g.close()
+    g = gpu_run(lbm, inputs.cylinder(600, 500, 20, 1000.0, eq=inputs.EQ_ENTROPIC), "f32")
+    assert g.info()["tile_shape"] == 5
+    g.close()
+
+
 def test_probe_series_matches_oracle(lbm):
     w = small_cylinder(re=5000.0)
     cfg = oracle_cfg(w)
