@@ -43,6 +43,8 @@ int fail(int code, const char* fmt, ...) {
     } while (0)
 
 constexpr int kGraphSteps = 32;      // steps per captured graph (even: buffers return)
+constexpr int kExportChunks = 8;     // row chunks of a host export (copies overlap the conversion)
+constexpr int kXferEvents = 16;      // events of one chunked transfer (>= Q planes, >= chunks, + 1)
 constexpr int kDefaultLog = 65536;
 // Default tile shapes, the fastest measured on GB300: FP32 and FP16 storage
 // (plain and deviation) stage 6-row tiles with 2 more in flight per block
@@ -143,6 +145,12 @@ struct lb_handle {
     // per call costs more than the copy itself
     double* stage;
     size_t stage_bytes;
+    // stream of the host copies of those transfers (created with the
+    // staging buffer) and the events that order them with the conversion
+    // kernels on the run's stream: chunk by chunk, so that one chunk's copy
+    // overlaps the conversion of the next (import) or the previous (export)
+    cudaStream_t copy_stream;
+    cudaEvent_t xfer_ev[kXferEvents];
     unsigned long long* newton_stats;
     // completion ticket of the stream-collide blocks; tile shape of K1
     unsigned* ticket;
@@ -474,6 +482,12 @@ void lb_destroy(lb_handle* h) {
     if (h->h_err) cudaFreeHost(h->h_err);
     if (h->err_ev) cudaEventDestroy(h->err_ev);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    if (h->copy_stream) {
+        cudaStreamSynchronize(h->copy_stream);
+        for (cudaEvent_t e : h->xfer_ev)
+            if (e) cudaEventDestroy(e);
+        cudaStreamDestroy(h->copy_stream);
+    }
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -623,6 +637,10 @@ int lb_create(int lattice, int nx, int ny, int equilibrium, double nu, double de
 // The handle's staging buffer, at least `bytes` long (the previous calls that
 // used it have synchronised with the stream).
 static int staging(lb_handle* h, size_t bytes, double** out) {
+    if (!h->copy_stream) {
+        CK(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+        for (cudaEvent_t& e : h->xfer_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
     if (h->stage_bytes < bytes) {
         if (h->stage) cudaFree(h->stage);
         h->stage = nullptr;
@@ -657,44 +675,66 @@ int lb_init_equilibrium(lb_handle* h, const double* rho, const double* ux, const
     return LB_OK;
 }
 
+// The state is uploaded plane by plane on the copy stream; the run's stream
+// converts plane i (k_import) while plane i + 1 is in flight.  The copies
+// start after the work already queued on the run's stream.
 int lb_set_state(lb_handle* h, const double* f) {
     if (!h || !f) return fail(LB_ERR_ARG, "NULL argument");
     const long long N = (long long)h->nx * h->ny;
     const size_t nb = (size_t)h->Q * N * sizeof(double);
     double* d = nullptr;
     if (int rc = staging(h, nb, &d)) return rc;
-    CK(cudaMemcpyAsync(d, f, nb, cudaMemcpyHostToDevice, h->stream));
     Params P = make_params(h, 1 - h->cur, true);
-    CK(h->L.import_state(P, d, h->stream));
+    CK(cudaEventRecord(h->xfer_ev[kXferEvents - 1], h->stream));
+    CK(cudaStreamWaitEvent(h->copy_stream, h->xfer_ev[kXferEvents - 1], 0));
+    for (int i = 0; i < h->Q; i++) {
+        CK(cudaMemcpyAsync(d + i * N, f + i * N, (size_t)N * sizeof(double), cudaMemcpyHostToDevice,
+                           h->copy_stream));
+        CK(cudaEventRecord(h->xfer_ev[i], h->copy_stream));
+        CK(cudaStreamWaitEvent(h->stream, h->xfer_ev[i], 0));
+        CK(h->L.import_state(P, d, i, i + 1, h->stream));
+    }
     CK(cudaStreamSynchronize(h->stream));
     h->prestream = true;
     return LB_OK;
 }
 
+// Host exports go in row chunks: the run's stream converts chunk c
+// (k_export over its sites) while the copy stream moves chunk c - 1 to the
+// host; each field (mode 0: each population plane) is copied per chunk.
 static int export_fields(lb_handle* h, int mode, double* o0, double* o1, double* o2, double* o3,
                          int on_device) {
     const long long N = (long long)h->nx * h->ny;
-    const int nout = mode == 0 ? h->Q : (mode == 1 ? 4 : 1);
-    double* outs[4] = {o0, o1, o2, o3};
     if (on_device) {
         Params P = make_params(h, h->cur, h->prestream);
-        CK(h->L.export_state(P, mode, o0, o1, o2, o3, h->stream));
+        CK(h->L.export_state(P, mode, o0, o1, o2, o3, 0, N, h->stream));
         return LB_OK;
     }
     double* d = nullptr;
-    const size_t per = (size_t)N * sizeof(double) * (mode == 0 ? h->Q : 1);
-    if (int rc = staging(h, per * (mode == 1 ? 4 : 1), &d)) return rc;
+    const int planes = mode == 0 ? h->Q : 1;   // planes of N values per output field
+    if (int rc = staging(h, (size_t)N * sizeof(double) * (mode == 0 ? h->Q : (mode == 1 ? 4 : 1)), &d))
+        return rc;
     Params P = make_params(h, h->cur, h->prestream);
-    double* d0 = d;
-    double* d1 = (mode == 1 && o1) ? d + N : nullptr;
-    double* d2 = (mode == 1 && o2) ? d + 2 * N : nullptr;
-    double* d3 = (mode == 1 && o3) ? d + 3 * N : nullptr;
-    CK(h->L.export_state(P, mode, d0, d1, d2, d3, h->stream));
-    double* dd[4] = {d0, d1, d2, d3};
-    for (int i = 0; i < (mode == 1 ? 4 : 1); i++)
-        if (outs[i] && dd[i]) CK(cudaMemcpyAsync(outs[i], dd[i], per, cudaMemcpyDeviceToHost, h->stream));
+    double* outs[4] = {o0, mode == 1 ? o1 : nullptr, mode == 1 ? o2 : nullptr, mode == 1 ? o3 : nullptr};
+    double* dd[4] = {d, outs[1] ? d + N : nullptr, outs[2] ? d + 2 * N : nullptr,
+                     outs[3] ? d + 3 * N : nullptr};
+    const int chunks = std::min(kExportChunks, h->ny);
+    const int rows = (h->ny + chunks - 1) / chunks;
+    for (int c = 0; c * rows < h->ny; c++) {
+        const long long s0 = (long long)c * rows * h->nx;
+        const long long s1 = std::min<long long>((long long)(c + 1) * rows, h->ny) * h->nx;
+        CK(h->L.export_state(P, mode, dd[0], dd[1], dd[2], dd[3], s0, s1, h->stream));
+        CK(cudaEventRecord(h->xfer_ev[c], h->stream));
+        CK(cudaStreamWaitEvent(h->copy_stream, h->xfer_ev[c], 0));
+        for (int j = 0; j < 4; j++) {
+            if (!outs[j] || !dd[j]) continue;
+            for (int q = 0; q < planes; q++)
+                CK(cudaMemcpyAsync(outs[j] + q * N + s0, dd[j] + q * N + s0, (size_t)(s1 - s0) * sizeof(double),
+                                   cudaMemcpyDeviceToHost, h->copy_stream));
+        }
+    }
+    CK(cudaStreamSynchronize(h->copy_stream));
     CK(cudaStreamSynchronize(h->stream));
-    (void)nout;
     return LB_OK;
 }
 

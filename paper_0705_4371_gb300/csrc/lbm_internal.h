@@ -16,9 +16,11 @@ struct Launchers {
     cudaError_t (*select)(const Params&, int stage_cap, int mode, cudaStream_t);
     cudaError_t (*init_eq)(const Params&, const double* rho, const double* ux, const double* uy,
                            const double* e2, cudaStream_t);
-    cudaError_t (*import_state)(const Params&, const double* f, cudaStream_t);
+    // planes [i0, i1) of an FP64 state [Q][ny][nx] -> storage
+    cudaError_t (*import_state)(const Params&, const double* f, int i0, int i1, cudaStream_t);
+    // sites [s0, s1) (index y nx + x) of the pre-collision state, exported
     cudaError_t (*export_state)(const Params&, int mode, double*, double*, double*, double*,
-                                cudaStream_t);
+                                long long s0, long long s1, cudaStream_t);
     cudaError_t (*set_smem)(int stage_cap);
     // slab ghost exchange: column col of field <-> packed buffer [3][ny]
     cudaError_t (*ghost)(const Params&, void* field, int col, int right, void* buf, int dir, cudaStream_t);

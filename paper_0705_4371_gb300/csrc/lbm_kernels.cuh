@@ -1854,9 +1854,9 @@ __global__ void k_init_eq(const __grid_constant__ Params P, const double* rho, c
     for (int i = 0; i < L::Q; i++) Store<S>::store(P.dst, i * P.plane + o, gs[i]);
 }
 
-// FP64 populations [Q][ny][nx] -> deviation storage.
+// FP64 populations [Q][ny][nx] -> deviation storage, planes [i0, i1).
 template <typename L, typename S>
-__global__ void k_import(const __grid_constant__ Params P, const double* f) {
+__global__ void k_import(const __grid_constant__ Params P, const double* f, int i0, int i1) {
     const long long N = (long long)P.nx * P.ny;
     const long long sid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (sid >= N) return;
@@ -1868,23 +1868,25 @@ __global__ void k_import(const __grid_constant__ Params P, const double* f) {
         // FP64 storage: a copy (no FP64 arithmetic)
 #pragma unroll
         for (int i = 0; i < L::Q; i++)
-            Store<S>::store(P.dst, i * P.plane + o, (T)(solid ? 0.0 : f[i * N + sid]));
+            if (i >= i0 && i < i1) Store<S>::store(P.dst, i * P.plane + o, (T)(solid ? 0.0 : f[i * N + sid]));
         return;
     }
 #pragma unroll
     for (int i = 0; i < L::Q; i++)
-        Store<S>::store(P.dst, i * P.plane + o, solid ? T(0) : dev_of_f64<L, S>(P, i, f[i * N + sid]));
+        if (i >= i0 && i < i1)
+            Store<S>::store(P.dst, i * P.plane + o, solid ? T(0) : dev_of_f64<L, S>(P, i, f[i * N + sid]));
 }
 
-// Pre-collision state of the current step (gather of src), exported as
-// mode 0: populations f [Q][ny][nx]; 1: rho, ux, uy, 2E; 2: exact dS.
+// Pre-collision state of the current step (gather of src) at sites
+// [s0, s1), exported as mode 0: populations f [Q][ny][nx]; 1: rho, ux, uy,
+// 2E; 2: exact dS (outputs indexed by the site's index y nx + x).
 template <typename L, typename S, int EQ>
 __global__ void k_export(const __grid_constant__ Params P, int mode, double* o0, double* o1, double* o2,
-                         double* o3) {
+                         double* o3, long long s0, long long s1) {
     using T = typename Store<S>::T;
     const long long N = (long long)P.nx * P.ny;
-    const long long sid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (sid >= N) return;
+    const long long sid = s0 + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (sid >= s1) return;
     const int x = (int)(sid % P.nx), y = (int)(sid / P.nx);
     if (is_solid(P, x, y)) {
         if (mode == 0) for (int i = 0; i < L::Q; i++) o0[i * N + sid] = 0.0;
@@ -2105,15 +2107,17 @@ struct LaunchImpl {
         k_init_eq<L, S, EQ><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(P, rho, ux, uy, e2);
         return cudaGetLastError();
     }
-    static cudaError_t import_state(const Params& P, const double* f, cudaStream_t st) {
+    static cudaError_t import_state(const Params& P, const double* f, int i0, int i1, cudaStream_t st) {
         const long long N = (long long)P.nx * P.ny;
-        k_import<L, S><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(P, f);
+        if (i0 < 0 || i1 > L::Q || i0 >= i1 || N <= 0) return cudaErrorInvalidValue;
+        k_import<L, S><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(P, f, i0, i1);
         return cudaGetLastError();
     }
     static cudaError_t export_state(const Params& P, int mode, double* o0, double* o1, double* o2,
-                                    double* o3, cudaStream_t st) {
+                                    double* o3, long long s0, long long s1, cudaStream_t st) {
         const long long N = (long long)P.nx * P.ny;
-        k_export<L, S, EQ><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(P, mode, o0, o1, o2, o3);
+        if (s0 < 0 || s1 > N || s0 >= s1) return cudaErrorInvalidValue;
+        k_export<L, S, EQ><<<(unsigned)((s1 - s0 + 255) / 256), 256, 0, st>>>(P, mode, o0, o1, o2, o3, s0, s1);
         return cudaGetLastError();
     }
     static cudaError_t ghost(const Params& P, void* field, int col, int right, void* buf, int dir,
