@@ -157,13 +157,27 @@ int lb_set_state(lb_handle* h, const double* f);
  * and the call returns the sticky status of work already completed. */
 int lb_step(lb_handle* h, int n);
 
-/* Wait for all queued work; return the sticky status. */
+/* Wait for all queued work (steps and asynchronous transfers); return the
+ * sticky status. */
 int lb_sync(lb_handle* h);
 
 /* Moments of the current pre-collision state: rho, u_x, u_y and 2E (each
  * [ny][nx] FP64; uy and e2 may be NULL).  on_device != 0: the pointers are
  * device pointers and the call does not synchronise. */
 int lb_moments(lb_handle* h, double* rho, double* ux, double* uy, double* e2, int on_device);
+
+/* Asynchronous forms of lb_set_state and of lb_moments with host arrays:
+ * the call queues the transfer (and its conversion) behind the work already
+ * queued and returns; f must stay unchanged, and rho, ux, uy, e2 hold the
+ * moments, only after lb_sync (or a synchronous call of the same kind).
+ * Uploads and downloads use separate copy streams and staging memory, so a
+ * state upload queued after lb_moments_async overlaps that download (the
+ * serving loop set_state_async, step, moments_async).  Host arrays in pinned
+ * memory (cudaHostAlloc) make the copies truly asynchronous; with pageable
+ * memory the calls are correct but the driver serialises the copies.
+ * Results equal those of the synchronous calls bit for bit. */
+int lb_set_state_async(lb_handle* h, const double* f);
+int lb_moments_async(lb_handle* h, double* rho, double* ux, double* uy, double* e2);
 
 /* Sites that took the Ehrenfests' step in the last completed step (order
  * unspecified).  idx: host array of cap ints; *count receives the number

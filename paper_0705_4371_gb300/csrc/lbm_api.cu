@@ -145,12 +145,19 @@ struct lb_handle {
     // per call costs more than the copy itself
     double* stage;
     size_t stage_bytes;
-    // stream of the host copies of those transfers (created with the
-    // staging buffer) and the events that order them with the conversion
-    // kernels on the run's stream: chunk by chunk, so that one chunk's copy
-    // overlaps the conversion of the next (import) or the previous (export)
-    cudaStream_t copy_stream;
-    cudaEvent_t xfer_ev[kXferEvents];
+    // streams of the host copies of those transfers (created with the
+    // staging buffers), uploads and downloads apart, and the events that
+    // order them with the conversion kernels on the run's stream: chunk by
+    // chunk, so that one chunk's copy overlaps the conversion of the next
+    // (import) or the previous (export).  Downloads have staging of their own
+    // (stage_out), so an upload can overlap a download; d2h_done marks the
+    // end of the last download, which the next export waits for before
+    // overwriting stage_out.
+    cudaStream_t copy_stream, d2h_stream;
+    cudaEvent_t xfer_ev[kXferEvents], out_ev[kXferEvents], d2h_done;
+    double* stage_out;
+    size_t stage_out_bytes;
+    bool d2h_pending;
     unsigned long long* newton_stats;
     // completion ticket of the stream-collide blocks; tile shape of K1
     unsigned* ticket;
@@ -484,10 +491,16 @@ void lb_destroy(lb_handle* h) {
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     if (h->copy_stream) {
         cudaStreamSynchronize(h->copy_stream);
+        cudaStreamSynchronize(h->d2h_stream);
         for (cudaEvent_t e : h->xfer_ev)
             if (e) cudaEventDestroy(e);
+        for (cudaEvent_t e : h->out_ev)
+            if (e) cudaEventDestroy(e);
+        if (h->d2h_done) cudaEventDestroy(h->d2h_done);
         cudaStreamDestroy(h->copy_stream);
+        cudaStreamDestroy(h->d2h_stream);
     }
+    if (h->stage_out) cudaFree(h->stage_out);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -636,11 +649,36 @@ int lb_create(int lattice, int nx, int ny, int equilibrium, double nu, double de
 
 // The handle's staging buffer, at least `bytes` long (the previous calls that
 // used it have synchronised with the stream).
-static int staging(lb_handle* h, size_t bytes, double** out) {
+static int copy_streams(lb_handle* h) {
     if (!h->copy_stream) {
         CK(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&h->d2h_stream, cudaStreamNonBlocking));
         for (cudaEvent_t& e : h->xfer_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        for (cudaEvent_t& e : h->out_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&h->d2h_done, cudaEventDisableTiming));
     }
+    return LB_OK;
+}
+
+// Download staging (exports), at least `bytes` long; a previous download
+// may still read it (the caller orders its kernels after d2h_done).
+static int staging_out(lb_handle* h, size_t bytes, double** out) {
+    if (int rc = copy_streams(h)) return rc;
+    if (h->stage_out_bytes < bytes) {
+        CK(cudaStreamSynchronize(h->d2h_stream));
+        if (h->stage_out) cudaFree(h->stage_out);
+        h->stage_out = nullptr;
+        h->stage_out_bytes = 0;
+        const size_t full = (size_t)std::max(h->Q, 4) * h->nx * h->ny * sizeof(double);
+        CK(cudaMalloc(&h->stage_out, std::max(bytes, full)));
+        h->stage_out_bytes = std::max(bytes, full);
+    }
+    *out = h->stage_out;
+    return LB_OK;
+}
+
+static int staging(lb_handle* h, size_t bytes, double** out) {
+    if (int rc = copy_streams(h)) return rc;
     if (h->stage_bytes < bytes) {
         if (h->stage) cudaFree(h->stage);
         h->stage = nullptr;
@@ -677,12 +715,14 @@ int lb_init_equilibrium(lb_handle* h, const double* rho, const double* ux, const
 
 // The state is uploaded plane by plane on the copy stream; the run's stream
 // converts plane i (k_import) while plane i + 1 is in flight.  The copies
-// start after the work already queued on the run's stream.
-int lb_set_state(lb_handle* h, const double* f) {
+// start after the work already queued on the run's stream (an earlier
+// upload's conversions read the same staging).
+static int set_state(lb_handle* h, const double* f, bool async) {
     if (!h || !f) return fail(LB_ERR_ARG, "NULL argument");
     const long long N = (long long)h->nx * h->ny;
     const size_t nb = (size_t)h->Q * N * sizeof(double);
     double* d = nullptr;
+    if (h->stage_bytes < nb && h->copy_stream) CK(cudaStreamSynchronize(h->stream));
     if (int rc = staging(h, nb, &d)) return rc;
     Params P = make_params(h, 1 - h->cur, true);
     CK(cudaEventRecord(h->xfer_ev[kXferEvents - 1], h->stream));
@@ -694,16 +734,20 @@ int lb_set_state(lb_handle* h, const double* f) {
         CK(cudaStreamWaitEvent(h->stream, h->xfer_ev[i], 0));
         CK(h->L.import_state(P, d, i, i + 1, h->stream));
     }
-    CK(cudaStreamSynchronize(h->stream));
     h->prestream = true;
+    if (!async) CK(cudaStreamSynchronize(h->stream));
     return LB_OK;
 }
 
+int lb_set_state(lb_handle* h, const double* f) { return set_state(h, f, false); }
+int lb_set_state_async(lb_handle* h, const double* f) { return set_state(h, f, true); }
+
 // Host exports go in row chunks: the run's stream converts chunk c
-// (k_export over its sites) while the copy stream moves chunk c - 1 to the
-// host; each field (mode 0: each population plane) is copied per chunk.
+// (k_export over its sites) while the download stream moves chunk c - 1 to
+// the host; each field (mode 0: each population plane) is copied per chunk.
+// The kernels first wait for the previous download out of the same staging.
 static int export_fields(lb_handle* h, int mode, double* o0, double* o1, double* o2, double* o3,
-                         int on_device) {
+                         int on_device, bool async = false) {
     const long long N = (long long)h->nx * h->ny;
     if (on_device) {
         Params P = make_params(h, h->cur, h->prestream);
@@ -712,8 +756,9 @@ static int export_fields(lb_handle* h, int mode, double* o0, double* o1, double*
     }
     double* d = nullptr;
     const int planes = mode == 0 ? h->Q : 1;   // planes of N values per output field
-    if (int rc = staging(h, (size_t)N * sizeof(double) * (mode == 0 ? h->Q : (mode == 1 ? 4 : 1)), &d))
+    if (int rc = staging_out(h, (size_t)N * sizeof(double) * (mode == 0 ? h->Q : (mode == 1 ? 4 : 1)), &d))
         return rc;
+    if (h->d2h_pending) CK(cudaStreamWaitEvent(h->stream, h->d2h_done, 0));
     Params P = make_params(h, h->cur, h->prestream);
     double* outs[4] = {o0, mode == 1 ? o1 : nullptr, mode == 1 ? o2 : nullptr, mode == 1 ? o3 : nullptr};
     double* dd[4] = {d, outs[1] ? d + N : nullptr, outs[2] ? d + 2 * N : nullptr,
@@ -724,17 +769,21 @@ static int export_fields(lb_handle* h, int mode, double* o0, double* o1, double*
         const long long s0 = (long long)c * rows * h->nx;
         const long long s1 = std::min<long long>((long long)(c + 1) * rows, h->ny) * h->nx;
         CK(h->L.export_state(P, mode, dd[0], dd[1], dd[2], dd[3], s0, s1, h->stream));
-        CK(cudaEventRecord(h->xfer_ev[c], h->stream));
-        CK(cudaStreamWaitEvent(h->copy_stream, h->xfer_ev[c], 0));
+        CK(cudaEventRecord(h->out_ev[c], h->stream));
+        CK(cudaStreamWaitEvent(h->d2h_stream, h->out_ev[c], 0));
         for (int j = 0; j < 4; j++) {
             if (!outs[j] || !dd[j]) continue;
             for (int q = 0; q < planes; q++)
                 CK(cudaMemcpyAsync(outs[j] + q * N + s0, dd[j] + q * N + s0, (size_t)(s1 - s0) * sizeof(double),
-                                   cudaMemcpyDeviceToHost, h->copy_stream));
+                                   cudaMemcpyDeviceToHost, h->d2h_stream));
         }
     }
-    CK(cudaStreamSynchronize(h->copy_stream));
-    CK(cudaStreamSynchronize(h->stream));
+    CK(cudaEventRecord(h->d2h_done, h->d2h_stream));
+    h->d2h_pending = true;
+    if (!async) {
+        CK(cudaStreamSynchronize(h->d2h_stream));
+        CK(cudaStreamSynchronize(h->stream));
+    }
     return LB_OK;
 }
 
@@ -746,6 +795,11 @@ int lb_get_state(lb_handle* h, double* f) {
 int lb_moments(lb_handle* h, double* rho, double* ux, double* uy, double* e2, int on_device) {
     if (!h || !rho || !ux) return fail(LB_ERR_ARG, "NULL argument");
     return export_fields(h, 1, rho, ux, uy, e2, on_device);
+}
+
+int lb_moments_async(lb_handle* h, double* rho, double* ux, double* uy, double* e2) {
+    if (!h || !rho || !ux) return fail(LB_ERR_ARG, "NULL argument");
+    return export_fields(h, 1, rho, ux, uy, e2, 0, true);
 }
 
 int lb_delta_s(lb_handle* h, double* ds, int on_device) {
@@ -788,6 +842,10 @@ int lb_step(lb_handle* h, int n) {
 int lb_sync(lb_handle* h) {
     if (!h) return fail(LB_ERR_ARG, "NULL handle");
     CK(cudaStreamSynchronize(h->stream));
+    if (h->copy_stream) {
+        CK(cudaStreamSynchronize(h->copy_stream));
+        CK(cudaStreamSynchronize(h->d2h_stream));
+    }
     return check_sticky(h, true);
 }
 

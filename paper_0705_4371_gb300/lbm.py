@@ -68,6 +68,8 @@ def load(path=None):
         "lb_step": ([H, ip], ip),
         "lb_sync": ([H], ip),
         "lb_moments": ([H, vp, vp, vp, vp, ip], ip),
+        "lb_set_state_async": ([H, vp], ip),
+        "lb_moments_async": ([H, vp, vp, vp, vp], ip),
         "lb_selected": ([H, vp, ip, C.POINTER(ip)], ip),
         "lb_counts": ([H, vp, ip], ip),
         "lb_set_probe": ([H, ip, ip], ip),
@@ -321,6 +323,18 @@ class Lattice:
         rho, ux, uy, e2 = (np.zeros(self.shape) for _ in range(4))
         _check(self.L.lb_moments(self.h, _ptr(rho), _ptr(ux), _ptr(uy), _ptr(e2), 0))
         return rho, ux, uy, e2
+
+    def set_state_async(self, f):
+        """lb_set_state_async: queue the upload of f (an FP64 [Q][ny][nx] C-contiguous array,
+        kept unchanged by the caller until sync())."""
+        assert f.dtype == np.float64 and f.flags.c_contiguous and f.size == self.q * self.nx * self.ny
+        _check(self.L.lb_set_state_async(self.h, _ptr(f)))
+
+    def moments_async(self, rho, ux, uy=None, e2=None):
+        """lb_moments_async into caller-provided FP64 [ny][nx] host arrays, valid after sync()."""
+        for a in (rho, ux, uy, e2):
+            assert a is None or (a.dtype == np.float64 and a.flags.c_contiguous and a.size == self.nx * self.ny)
+        _check(self.L.lb_moments_async(self.h, _ptr(rho), _ptr(ux), _ptr(uy), _ptr(e2)))
 
     def moments_device(self, rho_ptr, ux_ptr, uy_ptr=None, e2_ptr=None):
         """lb_moments into caller-provided device arrays (integer pointers; asynchronous)."""

@@ -272,6 +272,40 @@ def test_default_tile_shapes_follow_grid_size(lbm):
     g.close()
 
 
+@pytest.mark.parametrize("prec", ["f32dev", "f64"])
+def test_async_transfers_equal_the_synchronous_calls(lbm, prec):
+    # the serving loop (upload a state, step, download the moments) queued
+    # without waiting, its uploads overlapping the previous downloads, in
+    # pinned host memory: the same bits as the synchronous calls
+    import torch
+    w = inputs.cylinder(328, 150, 12, 5000.0)
+    rho, ux, uy = initial_fields(w, noise=1e-3)
+    src = gpu_run(lbm, w, prec)
+    src.init_equilibrium(rho, ux, uy)
+    states = []
+    for _ in range(4):
+        src.step(7)
+        states.append(src.get_state())
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    fs = [pin(f) for f in states]
+    sync_run, async_run = gpu_run(lbm, w, prec), gpu_run(lbm, w, prec)
+    want = []
+    for f in fs:
+        sync_run.set_state(f)
+        sync_run.step(3)
+        want.append(sync_run.moments())
+    got = [[pin(np.zeros((w.ny, w.nx))) for _ in range(4)] for _ in fs]
+    for f, out in zip(fs, got):
+        async_run.set_state_async(f)
+        async_run.step(3)
+        async_run.moments_async(*out)
+    async_run.sync()
+    for a, b in zip(want, got):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+    assert np.array_equal(sync_run.get_state(), async_run.get_state())
+
+
 def test_probe_series_matches_oracle(lbm):
     w = small_cylinder(re=5000.0)
     cfg = oracle_cfg(w)
