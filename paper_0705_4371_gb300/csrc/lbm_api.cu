@@ -152,12 +152,14 @@ struct lb_handle {
     // (import) or the previous (export).  Downloads have staging of their own
     // (stage_out), so an upload can overlap a download; d2h_done marks the
     // end of the last download, which the next export waits for before
-    // overwriting stage_out.
+    // overwriting stage_out, and imp_done the end of the last upload's
+    // conversions, the only readers of stage, which the next upload's
+    // copies wait for.
     cudaStream_t copy_stream, d2h_stream;
-    cudaEvent_t xfer_ev[kXferEvents], out_ev[kXferEvents], d2h_done;
+    cudaEvent_t xfer_ev[kXferEvents], out_ev[kXferEvents], d2h_done, imp_done;
     double* stage_out;
     size_t stage_out_bytes;
-    bool d2h_pending;
+    bool d2h_pending, imp_pending;
     unsigned long long* newton_stats;
     // completion ticket of the stream-collide blocks; tile shape of K1
     unsigned* ticket;
@@ -497,6 +499,7 @@ void lb_destroy(lb_handle* h) {
         for (cudaEvent_t e : h->out_ev)
             if (e) cudaEventDestroy(e);
         if (h->d2h_done) cudaEventDestroy(h->d2h_done);
+        if (h->imp_done) cudaEventDestroy(h->imp_done);
         cudaStreamDestroy(h->copy_stream);
         cudaStreamDestroy(h->d2h_stream);
     }
@@ -656,6 +659,7 @@ static int copy_streams(lb_handle* h) {
         for (cudaEvent_t& e : h->xfer_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         for (cudaEvent_t& e : h->out_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&h->d2h_done, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&h->imp_done, cudaEventDisableTiming));
     }
     return LB_OK;
 }
@@ -715,8 +719,10 @@ int lb_init_equilibrium(lb_handle* h, const double* rho, const double* ux, const
 
 // The state is uploaded plane by plane on the copy stream; the run's stream
 // converts plane i (k_import) while plane i + 1 is in flight.  The copies
-// start after the work already queued on the run's stream (an earlier
-// upload's conversions read the same staging).
+// wait for the previous upload's conversions (they read the same staging;
+// the first upload waits for all the work queued so far), not for the
+// steps and exports queued after them, so that in a serving loop the next
+// upload runs while the run steps and downloads.
 static int set_state(lb_handle* h, const double* f, bool async) {
     if (!h || !f) return fail(LB_ERR_ARG, "NULL argument");
     const long long N = (long long)h->nx * h->ny;
@@ -725,8 +731,12 @@ static int set_state(lb_handle* h, const double* f, bool async) {
     if (h->stage_bytes < nb && h->copy_stream) CK(cudaStreamSynchronize(h->stream));
     if (int rc = staging(h, nb, &d)) return rc;
     Params P = make_params(h, 1 - h->cur, true);
-    CK(cudaEventRecord(h->xfer_ev[kXferEvents - 1], h->stream));
-    CK(cudaStreamWaitEvent(h->copy_stream, h->xfer_ev[kXferEvents - 1], 0));
+    if (h->imp_pending) {
+        CK(cudaStreamWaitEvent(h->copy_stream, h->imp_done, 0));
+    } else {
+        CK(cudaEventRecord(h->xfer_ev[kXferEvents - 1], h->stream));
+        CK(cudaStreamWaitEvent(h->copy_stream, h->xfer_ev[kXferEvents - 1], 0));
+    }
     for (int i = 0; i < h->Q; i++) {
         CK(cudaMemcpyAsync(d + i * N, f + i * N, (size_t)N * sizeof(double), cudaMemcpyHostToDevice,
                            h->copy_stream));
@@ -734,6 +744,8 @@ static int set_state(lb_handle* h, const double* f, bool async) {
         CK(cudaStreamWaitEvent(h->stream, h->xfer_ev[i], 0));
         CK(h->L.import_state(P, d, i, i + 1, h->stream));
     }
+    CK(cudaEventRecord(h->imp_done, h->stream));
+    h->imp_pending = true;
     h->prestream = true;
     if (!async) CK(cudaStreamSynchronize(h->stream));
     return LB_OK;
