@@ -167,9 +167,11 @@ int lb_sync(lb_handle* h);
 int lb_moments(lb_handle* h, double* rho, double* ux, double* uy, double* e2, int on_device);
 
 /* Asynchronous forms of lb_set_state and of lb_moments with host arrays:
- * the call queues the transfer (and its conversion) behind the work already
- * queued and returns; f must stay unchanged, and rho, ux, uy, e2 hold the
- * moments, only after lb_sync (or a synchronous call of the same kind).
+ * the call queues the transfer and returns.  The uploaded state replaces
+ * the run's after the work already queued (its copies may start earlier);
+ * the moments are those of the state after the work already queued.  f must
+ * stay unchanged, and rho, ux, uy, e2 hold the moments, only after lb_sync
+ * (or a synchronous call of the same kind).
  * Uploads and downloads use separate copy streams and staging memory, so a
  * state upload queued after lb_moments_async overlaps that download (the
  * serving loop set_state_async, step, moments_async).  Host arrays in pinned
