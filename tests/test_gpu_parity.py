@@ -306,6 +306,40 @@ def test_async_transfers_equal_the_synchronous_calls(lbm, prec):
     assert np.array_equal(sync_run.get_state(), async_run.get_state())
 
 
+def test_async_transfers_mixed_with_synchronous_calls(lbm):
+    # D1Q3 (one row: one export chunk, three planes), asynchronous and
+    # synchronous calls interleaved without lb_sync, and a handle destroyed
+    # with transfers still queued
+    w = inputs.shock_tube()
+    rho, ux, _ = inputs.shock_tube_fields(w)
+    ref = gpu_run(lbm, w, "f64")
+    ref.init_equilibrium(rho, ux)
+    ref.step(40)
+    f = ref.get_state()
+    ref.step(40)
+    want = ref.moments()
+    g = gpu_run(lbm, w, "f64")
+    g.init_equilibrium(rho, ux)
+    g.set_state_async(f)
+    g.step(40)
+    got = g.moments()                       # synchronous, behind the queued upload
+    for x, y in zip(want, got):
+        assert np.array_equal(x, y)
+    out = [np.zeros((w.ny, w.nx)) for _ in range(4)]
+    g.moments_async(*out)
+    assert np.array_equal(g.get_state(), ref.get_state())   # synchronous export after an async one
+    g.sync()
+    for x, y in zip(want, out):
+        assert np.array_equal(x, y)
+    h = gpu_run(lbm, w, "f64")
+    h.set_state_async(f)
+    h.step(3)
+    tmp = [np.zeros((w.ny, w.nx)) for _ in range(4)]    # alive until the transfers end
+    h.moments_async(*tmp)
+    h.close()                               # waits for the queued transfers
+    assert np.isfinite(tmp[0]).all()
+
+
 def test_probe_series_matches_oracle(lbm):
     w = small_cylinder(re=5000.0)
     cfg = oracle_cfg(w)
