@@ -480,6 +480,11 @@ const char* lb_last_error(void) { return g_last_error.c_str(); }
 void lb_destroy(lb_handle* h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->copy_stream) {
+        // transfers still queued read or write the staging buffers freed below
+        cudaStreamSynchronize(h->copy_stream);
+        cudaStreamSynchronize(h->d2h_stream);
+    }
     drop_graphs(h);
     void* ptrs[] = {h->buf[0], h->buf[1], h->cand_key, h->cand_idx, h->cand_count, h->sel_idx,
                     h->sel_count, h->count_ring, h->probe_ring, h->d_step, h->d_err, h->replay_cnt,
@@ -492,8 +497,6 @@ void lb_destroy(lb_handle* h) {
     if (h->err_ev) cudaEventDestroy(h->err_ev);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     if (h->copy_stream) {
-        cudaStreamSynchronize(h->copy_stream);
-        cudaStreamSynchronize(h->d2h_stream);
         for (cudaEvent_t e : h->xfer_ev)
             if (e) cudaEventDestroy(e);
         for (cudaEvent_t e : h->out_ev)
