@@ -95,15 +95,17 @@ def bracketed_launch_ms(h, n):
 
 
 def kernel_source_hash():
-    """Hash of the sources the single-run stream-collide kernels are compiled
-    from (the device headers they include and their instantiation units; not
-    the host API, nor the batched kernel's header, which they do not include)."""
+    """Hash of the sources that decide the single-run stream-collide launch's
+    DRAM traffic: the device headers and instantiation units the kernels are
+    compiled from, and the host API (which sets the tile shape and the tiles'
+    claim order); not the batched kernel's header, which they do not include."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_0705_4371_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
         if name == "lbm_batch_kernels.cuh":
             continue
-        if name.endswith((".cuh", ".h")) or (name.startswith("lbm_kernels_") and name.endswith(".cu")):
+        if name.endswith((".cuh", ".h")) or name == "lbm_api.cu" or \
+                (name.startswith("lbm_kernels_") and name.endswith(".cu")):
             with open(os.path.join(csrc, name), "rb") as fh:
                 h.update(name.encode())
                 h.update(fh.read())

@@ -171,8 +171,10 @@ struct lb_handle {
     // tensor maps of the two population buffers (shared-memory-staged shapes)
     CUtensorMap tmap[2];
     unsigned* tile_counter;
-    // claim order of the staged shapes' tiles: boundary tiles first
+    // claim order of the staged shapes' tiles: boundary tiles first; two
+    // orders of tile_order_n claims, by the parity of the buffer read
     int* tile_order;
+    int tile_order_n;
     // slab of a run sharded in x: ghost columns on each side, global x of the
     // first owned column, global nx; the keys of the slab's best candidates;
     // the step's selection among the slab's sites (one replayed step)
@@ -239,7 +241,7 @@ Params make_params(const lb_handle* h, int src, bool prestream) {
     P.pend_count = h->pend_count;
     P.grid_blocks = h->grid_blocks;
     P.tile_counter = h->tile_counter;
-    P.tile_order = h->tile_order;
+    P.tile_order = h->tile_order ? h->tile_order + (src ? h->tile_order_n : 0) : nullptr;
     P.elbm = h->elbm ? 1 : 0;
     P.wall = h->bc.obstacle_wall;
     P.slab = h->slab;
@@ -364,8 +366,12 @@ int encode_tensor_map(const lb_handle* h, int b, int rows, int cols, CUtensorMap
 // interior tile: they are spread evenly over the first three quarters of
 // the claims, where they overlap interior tiles that keep the memory busy,
 // and the last claims are interior tiles of equal cost, so that the blocks
-// run out of work together.  Both kinds keep their row-major order.
-std::vector<int> staged_tile_order(const lb_handle* h, int rows, int cols) {
+// run out of work together.  Both kinds keep their row-major order, except
+// that with reverse the interior tiles come in the opposite order: the steps
+// that read buffer 1 use that order, so that each step starts on the tiles
+// the previous step wrote last, while they are still in L2 (4096 x 2048:
+// 75.2 k against 74.2 k MLUPS).
+std::vector<int> staged_tile_order(const lb_handle* h, int rows, int cols, bool reverse) {
     const int tiles_x = (h->nx + cols - 1) / cols, tiles_y = (h->ny + rows - 1) / rows;
     const lb_boundaries& b = h->bc;
     std::vector<int> slow, fast;
@@ -378,6 +384,7 @@ std::vector<int> staged_tile_order(const lb_handle* h, int rows, int cols) {
                                 y0 - 1 >= b.obstacle_y0 + b.obstacle_h);
             (clean ? fast : slow).push_back(ty * tiles_x + tx);
         }
+    if (reverse) std::reverse(fast.begin(), fast.end());
     const size_t n = slow.size() + fast.size();
     const size_t span = std::max(slow.size(), n * 3 / 4);   // claims the slow tiles are spread over
     std::vector<int> order;
@@ -400,7 +407,10 @@ int make_tensor_maps(lb_handle* h) {
         const int rc = encode_tensor_map(h, b, rows, cols, &h->tmap[b]);
         if (rc != LB_OK) return rc;
     }
-    const std::vector<int> order = staged_tile_order(h, rows, cols);
+    std::vector<int> order = staged_tile_order(h, rows, cols, false);
+    const std::vector<int> back = staged_tile_order(h, rows, cols, true);
+    h->tile_order_n = (int)order.size();
+    order.insert(order.end(), back.begin(), back.end());
     if (h->tile_order) cudaFree(h->tile_order);
     h->tile_order = nullptr;
     CK(cudaMalloc(&h->tile_order, order.size() * sizeof(int)));
